@@ -1,0 +1,144 @@
+"""Plant plausible mistakes in a copy of the oracle and check that its pins
+catch every one (CPU only).  The mutants are textual edits of oracle.c,
+compiled into a temporary directory; the real oracle is untouched."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import read_golden
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+
+def wide_range_f32(n, seed):
+    """Normal floats scaled by 2^e, e uniform in [-40, 40]: their running sums
+    need more than 53 bits, so double accumulation rounds."""
+    e = synth.uniform_i32(n, 81, seed=seed, stream=5).astype(np.float64) - 40
+    return (synth.normal_f32(n, seed=seed) * np.exp2(e)).astype(np.float32)
+
+
+def meets_neumaier_bound(got, vals, excl):
+    """|got_k - exact_k| <= 2u|exact_k| + O(n u^2) sum|a| (u = 2^-53), with
+    exact_k from math.fsum (correctly rounded); plain double accumulation
+    fails it on wide-range data."""
+    vals = [float(v) for v in vals]
+    exact = np.array([math.fsum(vals[:k + (0 if excl else 1)]) for k in range(len(vals))])
+    den = np.cumsum(np.abs(vals))
+    if excl:
+        den = np.concatenate([[0.0], den[:-1]])
+    bound = 2.0 ** -52 * np.abs(exact) + 2.0 ** -90 * den
+    return bool(np.all(np.abs(np.asarray(got) - exact) <= bound))
+
+
+def pins_pass(lib) -> bool:
+    """A condensed run of the oracle's pins against `lib`."""
+    g = read_golden("definition_example.txt")
+    a = np.array(g["input"])
+    checks = [
+        oracle.scan_i32(a, lib=lib).tolist() == g["inclusive"],
+        oracle.scan_i32(a, True, lib=lib).tolist() == g["exclusive"],
+        oracle.scan_i64(a, lib=lib).tolist() == g["inclusive"],
+        oracle.scan_i64(a, True, lib=lib).tolist() == g["exclusive"],
+        oracle.scan_f32_ref(a, lib=lib).tolist() == g["inclusive"],
+        oracle.scan_f32_ref(a, True, lib=lib).tolist() == g["exclusive"],
+        oracle.rows_suffix_f32_ref(a.reshape(1, -1), lib=lib).ravel().tolist()
+        == g["suffix_inclusive"],
+        oracle.rows_suffix_f32_ref(a.reshape(1, -1), True, lib=lib).ravel().tolist()
+        == g["suffix_exclusive"],
+        oracle.seg_scan_i32(a, g["offsets"], lib=lib).tolist() == g["seg_inclusive"],
+        oracle.seg_scan_i32(a, g["offsets"], True, lib=lib).tolist() == g["seg_exclusive"],
+        oracle.seg_scan_f32_ref(a, g["offsets"], True, lib=lib).tolist() == g["seg_exclusive"],
+        oracle.seg_scan_i64(a, g["offsets"], True, lib=lib).tolist() == g["seg_exclusive"],
+    ]
+    n = 4096
+    k = (synth.unit_f32(n, seed=1).astype(np.float64) * 2 ** 24).astype(np.int64)
+    f = (k * 2.0 ** -24).astype(np.float32)
+    want = np.cumsum(k) * 2.0 ** -24
+    checks += [
+        np.array_equal(oracle.scan_f32_ref(f, lib=lib), want),
+        np.array_equal(oracle.abs_scan_f32(-f, lib=lib), want),
+        np.array_equal(oracle.abs_scan_f32(-f, True, lib=lib),
+                       np.concatenate([[0.0], want[:-1]])),
+        np.array_equal(oracle.rows_suffix_abs_f32(-f.reshape(1, -1), True, lib=lib).ravel(),
+                       np.concatenate([np.flip(np.cumsum(np.flip(k)))[1:], [0]]) * 2.0 ** -24),
+        np.array_equal(oracle.scan_f64_ref(f.astype(np.float64), lib=lib), want),
+        np.array_equal(oracle.scan_f32_plain_f64(f, lib=lib), want),
+        np.array_equal(oracle.rows_suffix_abs_f32(-f.reshape(1, -1), lib=lib).ravel(),
+                       np.flip(np.cumsum(np.flip(k))) * 2.0 ** -24),
+        np.array_equal(oracle.rows_suffix_f64_ref(f.reshape(2, -1).astype(np.float64),
+                                                  lib=lib),
+                       np.flip(np.cumsum(np.flip(k.reshape(2, -1), 1), 1), 1) * 2.0 ** -24),
+        np.array_equal(oracle.rows_suffix_f32_ref(f.reshape(4, -1), lib=lib),
+                       np.flip(np.cumsum(np.flip(k.reshape(4, -1), 1), 1), 1) * 2.0 ** -24),
+        np.array_equal(oracle.scan_f32_plain_f64(f, True, lib=lib),
+                       np.concatenate([[0.0], want[:-1]])),
+        np.array_equal(oracle.scan_f64_ref(f.astype(np.float64), True, lib=lib),
+                       np.concatenate([[0.0], want[:-1]])),
+        np.array_equal(oracle.seg_abs_scan_f32(-f, [0, 100, n], lib=lib)[:100],
+                       np.cumsum(k[:100]) * 2.0 ** -24),
+    ]
+    x = wide_range_f32(1500, seed=2)
+    x64 = synth.normal_f64(1500, seed=2)
+    for excl in (False, True):
+        for got, vals in ((oracle.scan_f32_ref(x, excl, lib=lib), x.astype(np.float64)),
+                          (oracle.scan_f64_ref(x64, excl, lib=lib), x64)):
+            checks.append(meets_neumaier_bound(got, vals, excl))
+    i = np.arange(1, 70001, dtype=np.int64)
+    checks.append(oracle.reduce_i32(i.astype(np.int32), lib=lib)
+                  == np.int64(i.sum() % (1 << 32)).astype(np.uint32).view(np.int32))
+    checks.append(oracle.reduce_i64(i, lib=lib) == i.sum())
+    return all(bool(c) for c in checks)
+
+
+MUTANTS = {
+    # (description): (original text, replacement text, occurrence index)
+    "i32 exclusive adds before writing": (
+        "            y[k] = (int32_t)run;\n            run += ak;",
+        "            run += ak;\n            y[k] = (int32_t)run;", 0),
+    "i64 dropped term": ("run += ak;", "run += ak & ~1ull;", 2),
+    "i64 reduce off by one": ("for (int64_t k = 0; k < n; ++k) s += (uint64_t)a[k];",
+                              "for (int64_t k = 1; k < n; ++k) s += (uint64_t)a[k];", 0),
+    "reduce i32 wrong sign": ("s += (uint32_t)a[k];", "s -= (uint32_t)a[k];", 0),
+    "neumaier wrong sign": ("acc->c += (acc->s - t) + x;", "acc->c -= (acc->s - t) + x;", 0),
+    "neumaier lost error term": ("acc->c += (x - t) + acc->s;", "acc->c += (x - t);", 0),
+    "f32 ref drops compensation in output": ("            y[k] = acc.s + acc.c;\n        }\n    }\n}\n\nvoid oracle_scan_f64_ref",
+                                             "            y[k] = acc.s;\n        }\n    }\n}\n\nvoid oracle_scan_f64_ref", 0),
+    "abs scan forgets fabs": ("neum_add(&acc, fabs((double)a[k]));\n        } else {",
+                              "neum_add(&acc, ((double)a[k]));\n        } else {", 0),
+    "segment bound off by one": ("if (e > b) oracle_scan_i32(a + b, y + b, e - b, exclusive);",
+                                 "if (e > b) oracle_scan_i32(a + b, y + b, e - b - 1, exclusive);", 0),
+    "segment uses next start": ("int64_t b = offsets[s], e = offsets[s + 1];\n        if (e > b) oracle_scan_f32_ref",
+                                "int64_t b = offsets[s + 1], e = offsets[s + 1];\n        if (e > b) oracle_scan_f32_ref", 0),
+    "suffix starts one early": ("for (int64_t i = cols - 1; i >= 0; --i) {", "for (int64_t i = cols - 2; i >= 0; --i) {", 0),
+    "suffix f64 transposed index": ("const double* ar = a + r * cols;", "const double* ar = a + r;", 0),
+    "plain double exclusive shifted": ("y[k] = run;\n            run += (double)a[k];",
+                                       "run += (double)a[k];\n            y[k] = run;", 0),
+}
+
+
+def make_mutant(tmp_path, name, old, new, which):
+    src = open(SRC).read()
+    pos = -1
+    for _ in range(which + 1):
+        pos = src.find(old, pos + 1)
+        assert pos >= 0, f"mutation site not found: {name}"
+    mutated = src[:pos] + new + src[pos + len(old):]
+    cpath = tmp_path / "mutant.c"
+    cpath.write_text(mutated)
+    so = oracle.build(force=True, src=str(cpath), out=str(tmp_path / "libmutant.so"))
+    return oracle.load_library(so)
+
+
+def test_real_oracle_passes_condensed_pins():
+    assert pins_pass(None)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    old, new, which = MUTANTS[name]
+    lib = make_mutant(tmp_path, name, old, new, which)
+    assert not pins_pass(lib), f"mutant survived: {name}"
