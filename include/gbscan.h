@@ -1,0 +1,205 @@
+/*
+ * gbscan.h — C ABI of the GB300 (sm_103a) prefix-sum library.
+ *
+ * The operation (Zhang, Wang, Ross, "Parallel Prefix Sum with SIMD", ADMS'20,
+ * Section 1): given [a_0, ..., a_{n-1}] and the operator +, the inclusive scan
+ * is y_k = a_0 + ... + a_k; the exclusive scan is y_0 = 0, y_k = a_0 + ... +
+ * a_{k-1}.  The paper's algorithms are multithreaded two-pass CPU schemes
+ * (Section 2.1, Figure 1) and in-register SIMD scans (Section 3, Listing 1);
+ * this library computes the same result on the GPU with a single-pass chained
+ * scan with decoupled look-back, and keeps a two-pass reduce-then-scan (the
+ * paper's "Accumulate + Prefix Sum", Figure 1b) as a comparison.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named in/out/offsets/grad_* and the workspace are DEVICE
+ *    pointers owned by the caller.  The library allocates nothing.
+ *  - All work is enqueued on `stream` and is asynchronous; nothing blocks
+ *    except scan_get_device_status().
+ *  - `out == in` (in place, the paper's default, Section 2) is allowed; any
+ *    other overlap of in and out returns GBSCAN_ERR_INVALID_ARG.
+ *  - Integer arithmetic wraps (two's complement); float results are rounded
+ *    sums whose rounding order depends on timing (float addition is not
+ *    associative, Section 1.1), so they may differ in the last bits between runs.
+ *  - n == 0 (or rows*cols == 0, or an empty segment list) is a no-op.
+ *  - Argument errors return a status synchronously and launch nothing.
+ *    Launch failures return GBSCAN_ERR_CUDA.  Errors found on the device (a
+ *    bounded wait that ran out, malformed segment offsets) are recorded in the
+ *    workspace and returned by scan_get_device_status().
+ *  - Full speed needs `in` and `out` 16-byte aligned; other alignments are
+ *    handled by a slower element-wise path.
+ *  - The library never aborts, traps or prints.
+ *
+ * Workspace: query its size with gbscan_workspace_size(), allocate it on the
+ * device, and zero it ONCE (gbscan_workspace_init or any memset to 0) before
+ * first use.  It may then be reused by any number of calls issued on one
+ * stream, including inside a captured CUDA graph: the kernels leave it ready
+ * for the next call.  Calls that overlap in time must use separate workspaces.
+ */
+#ifndef GBSCAN_H
+#define GBSCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBSCAN_ABI_VERSION 1
+
+typedef enum {
+    GBSCAN_OK = 0,
+    GBSCAN_ERR_INVALID_ARG = 1, /* null pointer, negative size, bad overlap, bad offsets */
+    GBSCAN_ERR_ALIGNMENT = 2,   /* pointer not aligned to its element size */
+    GBSCAN_ERR_WORKSPACE = 3,   /* workspace missing, misaligned or too small */
+    GBSCAN_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    GBSCAN_ERR_TIMEOUT = 5,     /* device: a bounded wait on another tile ran out */
+    GBSCAN_ERR_UNSUPPORTED = 6  /* size or option outside what is built */
+} gbscan_status;
+
+typedef enum {
+    GBSCAN_ALGO_AUTO = 0,        /* the single-pass scan */
+    GBSCAN_ALGO_SINGLE_PASS = 1, /* chained scan with decoupled look-back */
+    GBSCAN_ALGO_TWO_PASS = 2     /* reduce tiles, scan the tile sums, scan with offsets */
+} gbscan_algo;
+
+typedef enum {
+    GBSCAN_F32_PLAIN = 0,       /* all sums in fp32 */
+    GBSCAN_F32_COMPENSATED = 1  /* per-thread and carried prefixes as (hi, lo) TwoSum pairs */
+} gbscan_f32_mode;
+
+typedef enum { GBSCAN_I32 = 0, GBSCAN_I64 = 1, GBSCAN_F32 = 2, GBSCAN_F64 = 3 } gbscan_dtype;
+
+typedef enum {
+    GBSCAN_KIND_SCAN = 0,      /* one array, single-pass or two-pass */
+    GBSCAN_KIND_SEGMENTED = 1, /* CSR segments, one persistent launch */
+    GBSCAN_KIND_ROWS = 2       /* rows x cols, along the last dim, forward or reverse */
+} gbscan_kind;
+
+/* Bytes of workspace needed by any call of `kind` on `dtype` with n elements
+ * (and num_segments segments for GBSCAN_KIND_SEGMENTED), for every algorithm
+ * and every variant.  Writes *bytes; returns GBSCAN_ERR_INVALID_ARG for a null
+ * `bytes` or negative sizes and GBSCAN_ERR_UNSUPPORTED beyond the largest
+ * supported size (2^31 tiles, 2^31 - 1 segments). */
+gbscan_status gbscan_workspace_size(gbscan_dtype dtype, gbscan_kind kind, int64_t n,
+                                    int64_t num_segments, size_t* bytes);
+
+/* Zero a workspace on `stream` (cudaMemsetAsync).  Needed once per allocation. */
+gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * Plain scans of one contiguous array (Section 1 definition).
+ *   in, out   : device arrays of n elements (out == in allowed).
+ *   n         : element count, >= 0.
+ *   ws        : zeroed workspace of ws_bytes >= gbscan_workspace_size(dtype, SCAN, n, 0).
+ *   algo      : GBSCAN_ALGO_AUTO / SINGLE_PASS (one launch) or TWO_PASS (three launches:
+ *               tile reduce, one-block scan of the tile sums, scan with offsets).
+ *   variant   : launch shape (threads, items per thread, pipeline stages), 0 = default;
+ *               see gbscan_num_variants / gbscan_variant_info.
+ *   mode      : (f32 only) plain fp32 or compensated two-sum carries.
+ */
+gbscan_status scan_inclusive_i32(const int32_t* in, int32_t* out, int64_t n, void* ws,
+                                 size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+gbscan_status scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, void* ws,
+                                 size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+gbscan_status scan_inclusive_i64(const int64_t* in, int64_t* out, int64_t n, void* ws,
+                                 size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+gbscan_status scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, void* ws,
+                                 size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+gbscan_status scan_inclusive_f32(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
+                                 void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+gbscan_status scan_exclusive_f32(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
+                                 void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+/* fp64 scans: used by the autograd layer for double-precision gradient checks. */
+gbscan_status scan_inclusive_f64(const double* in, double* out, int64_t n, void* ws,
+                                 size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+gbscan_status scan_exclusive_f64(const double* in, double* out, int64_t n, void* ws,
+                                 size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+
+/*
+ * Batched segmented scan (the Section 1 definition restarted at every segment
+ * start; segments are not in the paper).  One persistent launch over the flat
+ * array plus one small launch that locates each tile's first segment.
+ *   offsets      : device int64 CSR array of num_segments + 1 entries, monotone,
+ *                  offsets[0] = 0, offsets[num_segments] = n (the total length).
+ *                  Empty segments are allowed.  Malformed offsets are reported by
+ *                  scan_get_device_status() as GBSCAN_ERR_INVALID_ARG.
+ *   n            : total length (offsets[num_segments], which the caller knows).
+ *   exclusive    : 0 inclusive, 1 exclusive per segment (each segment starts at 0).
+ * No host synchronisation: the call can be captured in a CUDA graph.
+ */
+gbscan_status scan_segmented_batched_i32(const int32_t* in, int32_t* out, int64_t n,
+                                         const int64_t* offsets, int64_t num_segments,
+                                         int exclusive, void* ws, size_t ws_bytes, int variant,
+                                         cudaStream_t stream);
+gbscan_status scan_segmented_batched_f32(const float* in, float* out, int64_t n,
+                                         const int64_t* offsets, int64_t num_segments,
+                                         int exclusive, void* ws, size_t ws_bytes, int variant,
+                                         cudaStream_t stream);
+
+/*
+ * Row-wise scan along the last dimension of a row-major rows x cols array
+ * (torch.cumsum(x, -1)): y[r, i] = sum_{k <= i} x[r, k] (exclusive: k < i).
+ */
+gbscan_status scan_rows_f32(const float* in, float* out, int64_t rows, int64_t cols,
+                            int exclusive, void* ws, size_t ws_bytes, int variant,
+                            cudaStream_t stream);
+gbscan_status scan_rows_f64(const double* in, double* out, int64_t rows, int64_t cols,
+                            int exclusive, void* ws, size_t ws_bytes, int variant,
+                            cudaStream_t stream);
+
+/*
+ * Gradient of the row-wise scan: the reverse (suffix) scan of the incoming
+ * gradient along the last dim.  The forward y_k = sum_{i<=k} x_i has Jacobian
+ * dy_k/dx_i = [i <= k], so dx_i = sum_{k >= i} g_k; for the exclusive forward,
+ * dx_i = sum_{k > i} g_k.  grad_out and grad_in are rows x cols, row-major;
+ * grad_in == grad_out is allowed.
+ */
+gbscan_status scan_backward_f32(const float* grad_out, float* grad_in, int64_t rows, int64_t cols,
+                                int exclusive, void* ws, size_t ws_bytes, int variant,
+                                cudaStream_t stream);
+gbscan_status scan_backward_f64(const double* grad_out, double* grad_in, int64_t rows,
+                                int64_t cols, int exclusive, void* ws, size_t ws_bytes,
+                                int variant, cudaStream_t stream);
+
+/* Synchronises `stream`, returns the first device-side error recorded in the
+ * workspace since the last call (GBSCAN_OK if none) and clears it. */
+gbscan_status scan_get_device_status(void* ws, cudaStream_t stream);
+
+/* Test and tuning hooks, stored in the workspace header (not global state):
+ *   spin_limit_us : bound of every wait on another tile, 0 = default (200 ms).
+ *   drop_tile     : a tile index whose status is never published (-1 = none):
+ *                   its successor's wait runs out and records GBSCAN_ERR_TIMEOUT.
+ *   delay_ns_max  : before each status publication, sleep a pseudo-random
+ *                   0..delay_ns_max ns to reorder tile completion (0 = off). */
+gbscan_status gbscan_set_debug(void* ws, size_t ws_bytes, uint32_t spin_limit_us,
+                               int64_t drop_tile, uint32_t delay_ns_max, cudaStream_t stream);
+
+/* Launch shapes: number of variants for a (dtype, kind), and the shape of one:
+ * threads per block, items per thread, pipeline stages, tile elements. */
+int gbscan_num_variants(gbscan_dtype dtype, gbscan_kind kind);
+gbscan_status gbscan_variant_info(gbscan_dtype dtype, gbscan_kind kind, int variant,
+                                  int* threads, int* items, int* stages, int* tile);
+
+/* Device-to-device copy of `bytes` bytes with a vectorised copy kernel: the
+ * bandwidth reference the scan is measured against. */
+gbscan_status gbscan_copy(const void* src, void* dst, size_t bytes, cudaStream_t stream);
+
+const char* gbscan_status_string(gbscan_status status);
+int gbscan_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSCAN_H */

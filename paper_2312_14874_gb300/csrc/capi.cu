@@ -1,0 +1,414 @@
+// capi.cu — the C ABI declared in include/gbscan.h: argument checks, workspace
+// layout, and dispatch to the tile kernels.  Host code plus three small
+// kernels (segment locator, debug-field writer, copy reference).
+#include <cstdint>
+#include <cstring>
+
+#include "gbscan_launch.cuh"
+
+namespace gbscan {
+
+int device_sm_count(int device) {
+    static std::atomic<int> cache[64];
+    if (device >= 0 && device < 64) {
+        const int c = cache[device].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return 0;
+    if (device >= 0 && device < 64) cache[device].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
+// rec[t].aux = first segment whose start is >= t * tile (lower bound over the
+// offsets), for t = 0..num_tiles; the tile kernel marks the starts of
+// segments [rec[t].aux, rec[t+1].aux) as heads.  Also checks the CSR offsets.
+__global__ void segment_locate_kernel(const int64_t* offsets, int64_t num_segments, int64_t n,
+                                      int64_t tile, int64_t num_tiles, TileRecord* rec,
+                                      Header* hdr) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int64_t t = first; t <= num_tiles; t += stride) {
+        int64_t pos = t * tile;
+        if (pos > n) pos = n;
+        int64_t lo = 0, hi = num_segments + 1;
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (offsets[mid] < pos)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        rec[t].aux = static_cast<unsigned long long>(lo);
+    }
+    bool bad = false;
+    for (int64_t j = first; j < num_segments; j += stride)
+        if (offsets[j] > offsets[j + 1]) bad = true;
+    if (first == 0 && (offsets[0] != 0 || offsets[num_segments] != n)) bad = true;
+    if (bad) record_error(hdr, GBSCAN_ERR_INVALID_ARG, -1);
+}
+
+__global__ void set_debug_kernel(Header* hdr, uint32_t spin_limit_us, int64_t drop_tile,
+                                 uint32_t delay_ns_max) {
+    hdr->spin_limit_us = spin_limit_us;
+    hdr->drop_tile_plus1 = drop_tile < 0 ? 0 : drop_tile + 1;
+    hdr->delay_ns_max = delay_ns_max;
+}
+
+__global__ void __launch_bounds__(256) copy_kernel(const uint4* __restrict__ src,
+                                                   uint4* __restrict__ dst, int64_t n16) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+        const uint4 a = __ldcs(src + i), b = __ldcs(src + i + stride);
+        const uint4 c = __ldcs(src + i + 2 * stride), d = __ldcs(src + i + 3 * stride);
+        __stcs(dst + i, a);
+        __stcs(dst + i + stride, b);
+        __stcs(dst + i + 2 * stride, c);
+        __stcs(dst + i + 3 * stride, d);
+    }
+    for (; i < n16; i += stride) __stcs(dst + i, __ldcs(src + i));
+}
+
+namespace {
+
+constexpr size_t kHeaderBytes = sizeof(Header);
+constexpr int64_t kMaxTiles = (int64_t(1) << 31) - (int64_t(1) << 24);
+
+int min_tile(gbscan_dtype dt) {
+    return (dt == GBSCAN_I64 || dt == GBSCAN_F64) ? kMinTile8 : kMinTile4;
+}
+
+bool valid_dtype(int dt) { return dt >= GBSCAN_I32 && dt <= GBSCAN_F64; }
+
+// Records needed for n elements at tile size `tile`: one per tile plus the
+// segment locator's end sentinel.
+int64_t records_for(int64_t n, int tile) { return (n + tile - 1) / tile + 1; }
+
+gbscan_status check_ws(void* ws, size_t ws_bytes, int64_t records) {
+    if (ws == nullptr) return GBSCAN_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return GBSCAN_ERR_WORKSPACE;
+    if (ws_bytes < kHeaderBytes) return GBSCAN_ERR_WORKSPACE;
+    const uint64_t cap = (ws_bytes - kHeaderBytes) / sizeof(TileRecord);
+    if (static_cast<uint64_t>(records) > cap) return GBSCAN_ERR_WORKSPACE;
+    return GBSCAN_OK;
+}
+
+bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+    return a0 < b0 + bbytes && b0 < a0 + abytes;
+}
+
+// in/out checks shared by every entry point: null, alignment to the element
+// size, and overlap other than exact aliasing.
+gbscan_status check_io(const void* in, const void* out, int64_t n, size_t esz) {
+    if (in == nullptr || out == nullptr) return GBSCAN_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(in) % esz || reinterpret_cast<uintptr_t>(out) % esz)
+        return GBSCAN_ERR_ALIGNMENT;
+    const size_t bytes = static_cast<size_t>(n) * esz;
+    if (in != out && ranges_overlap(in, bytes, out, bytes)) return GBSCAN_ERR_INVALID_ARG;
+    return GBSCAN_OK;
+}
+
+gbscan_status from_cuda(cudaError_t e) { return e == cudaSuccess ? GBSCAN_OK : GBSCAN_ERR_CUDA; }
+
+Params make_params(const void* in, void* out, int64_t n, int tile, void* ws, size_t ws_bytes) {
+    Params p{};
+    p.in = in;
+    p.out = out;
+    p.n = n;
+    p.num_tiles = (n + tile - 1) / tile;
+    p.hdr = static_cast<Header*>(ws);
+    p.rec = reinterpret_cast<TileRecord*>(static_cast<unsigned char*>(ws) + kHeaderBytes);
+    p.rec_capacity = static_cast<int64_t>((ws_bytes - kHeaderBytes) / sizeof(TileRecord));
+    p.fast = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    return p;
+}
+
+gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n, size_t esz,
+                        int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                        cudaStream_t stream) {
+    if (n < 0) return GBSCAN_ERR_INVALID_ARG;
+    if (algo != GBSCAN_ALGO_AUTO && algo != GBSCAN_ALGO_SINGLE_PASS && algo != GBSCAN_ALGO_TWO_PASS)
+        return GBSCAN_ERR_INVALID_ARG;
+    if (variant < 0 || variant >= fam.num_variants) return GBSCAN_ERR_INVALID_ARG;
+    if (n == 0) return GBSCAN_OK;
+    gbscan_status st = check_io(in, out, n, esz);
+    if (st != GBSCAN_OK) return st;
+    const Variant& v = fam.variants[variant];
+    const int64_t tiles = (n + v.tile - 1) / v.tile;
+    if (tiles > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
+    st = check_ws(ws, ws_bytes, records_for(n, v.tile));
+    if (st != GBSCAN_OK) return st;
+    Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
+    p.exclusive = exclusive;
+    cudaGetLastError();  // clear a stale, non-sticky error of an earlier call
+    if (algo == GBSCAN_ALGO_TWO_PASS) {
+        if (!v.reduce || !v.scan_offset || !fam.scan_sums) return GBSCAN_ERR_UNSUPPORTED;
+        cudaError_t e = v.reduce(p, stream);
+        if (e == cudaSuccess) e = fam.scan_sums(p.rec, p.num_tiles, stream);
+        if (e == cudaSuccess) e = v.scan_offset(p, stream);
+        return from_cuda(e);
+    }
+    return from_cuda(v.single_pass(p, stream));
+}
+
+gbscan_status scan_rows_impl(const Family& fam, const void* in, void* out, int64_t rows,
+                             int64_t cols, size_t esz, int exclusive, void* ws, size_t ws_bytes,
+                             int variant, cudaStream_t stream) {
+    if (rows < 0 || cols < 0) return GBSCAN_ERR_INVALID_ARG;
+    if (variant < 0 || variant >= fam.num_variants) return GBSCAN_ERR_INVALID_ARG;
+    if (rows == 0 || cols == 0) return GBSCAN_OK;
+    if (rows > INT64_MAX / cols) return GBSCAN_ERR_UNSUPPORTED;
+    const int64_t n = rows * cols;
+    gbscan_status st = check_io(in, out, n, esz);
+    if (st != GBSCAN_OK) return st;
+    const Variant& v = fam.variants[variant];
+    if ((n + v.tile - 1) / v.tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
+    st = check_ws(ws, ws_bytes, records_for(n, v.tile));
+    if (st != GBSCAN_OK) return st;
+    Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
+    p.exclusive = exclusive;
+    p.cols = cols;
+    cudaGetLastError();
+    return from_cuda(v.single_pass(p, stream));
+}
+
+gbscan_status scan_seg_impl(const Family& fam, const void* in, void* out, int64_t n,
+                            const int64_t* offsets, int64_t num_segments, size_t esz,
+                            int exclusive, void* ws, size_t ws_bytes, int variant,
+                            cudaStream_t stream) {
+    if (n < 0 || num_segments < 0 || num_segments > INT32_MAX) return GBSCAN_ERR_INVALID_ARG;
+    if (variant < 0 || variant >= fam.num_variants) return GBSCAN_ERR_INVALID_ARG;
+    if (n == 0) return GBSCAN_OK;  // every segment is empty
+    if (num_segments == 0 || offsets == nullptr) return GBSCAN_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(offsets) % 8) return GBSCAN_ERR_ALIGNMENT;
+    gbscan_status st = check_io(in, out, n, esz);
+    if (st != GBSCAN_OK) return st;
+    const Variant& v = fam.variants[variant];
+    if ((n + v.tile - 1) / v.tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
+    st = check_ws(ws, ws_bytes, records_for(n, v.tile));
+    if (st != GBSCAN_OK) return st;
+    Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
+    p.exclusive = exclusive;
+    p.offsets = offsets;
+    p.num_segments = num_segments;
+    cudaGetLastError();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = device_sm_count(dev);
+    int64_t work = num_segments > p.num_tiles + 1 ? num_segments : p.num_tiles + 1;
+    int64_t blocks = (work + 255) / 256;
+    const int64_t max_blocks = static_cast<int64_t>(sms > 0 ? sms : 1) * 8;
+    if (blocks > max_blocks) blocks = max_blocks;
+    segment_locate_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
+        offsets, num_segments, n, v.tile, p.num_tiles, p.rec, p.hdr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return GBSCAN_ERR_CUDA;
+    return from_cuda(v.single_pass(p, stream));
+}
+
+const Family* family_for(gbscan_dtype dt, gbscan_kind kind) {
+    switch (kind) {
+    case GBSCAN_KIND_SCAN:
+        switch (dt) {
+        case GBSCAN_I32: return &family_scan_i32();
+        case GBSCAN_I64: return &family_scan_i64();
+        case GBSCAN_F32: return &family_scan_f32();
+        case GBSCAN_F64: return &family_scan_f64();
+        }
+        break;
+    case GBSCAN_KIND_SEGMENTED:
+        if (dt == GBSCAN_I32) return &family_seg_i32();
+        if (dt == GBSCAN_F32) return &family_seg_f32();
+        break;
+    case GBSCAN_KIND_ROWS:
+        if (dt == GBSCAN_F32) return &family_rows_f32();
+        if (dt == GBSCAN_F64) return &family_rows_f64();
+        break;
+    }
+    return nullptr;
+}
+
+}  // namespace
+}  // namespace gbscan
+
+using namespace gbscan;
+
+extern "C" {
+
+gbscan_status gbscan_workspace_size(gbscan_dtype dtype, gbscan_kind kind, int64_t n,
+                                    int64_t num_segments, size_t* bytes) {
+    if (bytes == nullptr || n < 0 || num_segments < 0 || !valid_dtype(dtype))
+        return GBSCAN_ERR_INVALID_ARG;
+    if (kind < GBSCAN_KIND_SCAN || kind > GBSCAN_KIND_ROWS) return GBSCAN_ERR_INVALID_ARG;
+    if (num_segments > INT32_MAX) return GBSCAN_ERR_UNSUPPORTED;
+    const int tile = min_tile(dtype);
+    if ((n + tile - 1) / tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
+    *bytes = kHeaderBytes + static_cast<size_t>(records_for(n, tile)) * sizeof(TileRecord);
+    return GBSCAN_OK;
+}
+
+gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (ws == nullptr || ws_bytes < kHeaderBytes) return GBSCAN_ERR_WORKSPACE;
+    return from_cuda(cudaMemsetAsync(ws, 0, ws_bytes, stream));
+}
+
+#define GBSCAN_FLAT(NAME, TYPE, FAMILY, EXCL)                                                  \
+    gbscan_status NAME(const TYPE* in, TYPE* out, int64_t n, void* ws, size_t ws_bytes,       \
+                       gbscan_algo algo, int variant, cudaStream_t stream) {                  \
+        return scan_flat(FAMILY(), in, out, n, sizeof(TYPE), EXCL, ws, ws_bytes, algo, variant, \
+                         stream);                                                             \
+    }
+
+GBSCAN_FLAT(scan_inclusive_i32, int32_t, family_scan_i32, 0)
+GBSCAN_FLAT(scan_exclusive_i32, int32_t, family_scan_i32, 1)
+GBSCAN_FLAT(scan_inclusive_i64, int64_t, family_scan_i64, 0)
+GBSCAN_FLAT(scan_exclusive_i64, int64_t, family_scan_i64, 1)
+GBSCAN_FLAT(scan_inclusive_f64, double, family_scan_f64, 0)
+GBSCAN_FLAT(scan_exclusive_f64, double, family_scan_f64, 1)
+
+static gbscan_status scan_f32_impl(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
+                                   int excl, void* ws, size_t ws_bytes, gbscan_algo algo,
+                                   int variant, cudaStream_t stream) {
+    if (mode != GBSCAN_F32_PLAIN && mode != GBSCAN_F32_COMPENSATED) return GBSCAN_ERR_INVALID_ARG;
+    const Family& fam = mode == GBSCAN_F32_COMPENSATED ? family_scan_f32c() : family_scan_f32();
+    return scan_flat(fam, in, out, n, sizeof(float), excl, ws, ws_bytes, algo, variant, stream);
+}
+
+gbscan_status scan_inclusive_f32(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
+                                 void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream) {
+    return scan_f32_impl(in, out, n, mode, 0, ws, ws_bytes, algo, variant, stream);
+}
+
+gbscan_status scan_exclusive_f32(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
+                                 void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream) {
+    return scan_f32_impl(in, out, n, mode, 1, ws, ws_bytes, algo, variant, stream);
+}
+
+gbscan_status scan_segmented_batched_i32(const int32_t* in, int32_t* out, int64_t n,
+                                         const int64_t* offsets, int64_t num_segments,
+                                         int exclusive, void* ws, size_t ws_bytes, int variant,
+                                         cudaStream_t stream) {
+    return scan_seg_impl(family_seg_i32(), in, out, n, offsets, num_segments, sizeof(int32_t),
+                         exclusive != 0, ws, ws_bytes, variant, stream);
+}
+
+gbscan_status scan_segmented_batched_f32(const float* in, float* out, int64_t n,
+                                         const int64_t* offsets, int64_t num_segments,
+                                         int exclusive, void* ws, size_t ws_bytes, int variant,
+                                         cudaStream_t stream) {
+    return scan_seg_impl(family_seg_f32(), in, out, n, offsets, num_segments, sizeof(float),
+                         exclusive != 0, ws, ws_bytes, variant, stream);
+}
+
+gbscan_status scan_rows_f32(const float* in, float* out, int64_t rows, int64_t cols,
+                            int exclusive, void* ws, size_t ws_bytes, int variant,
+                            cudaStream_t stream) {
+    return scan_rows_impl(family_rows_f32(), in, out, rows, cols, sizeof(float), exclusive != 0,
+                          ws, ws_bytes, variant, stream);
+}
+
+gbscan_status scan_rows_f64(const double* in, double* out, int64_t rows, int64_t cols,
+                            int exclusive, void* ws, size_t ws_bytes, int variant,
+                            cudaStream_t stream) {
+    return scan_rows_impl(family_rows_f64(), in, out, rows, cols, sizeof(double), exclusive != 0,
+                          ws, ws_bytes, variant, stream);
+}
+
+gbscan_status scan_backward_f32(const float* grad_out, float* grad_in, int64_t rows, int64_t cols,
+                                int exclusive, void* ws, size_t ws_bytes, int variant,
+                                cudaStream_t stream) {
+    return scan_rows_impl(family_rows_rev_f32(), grad_out, grad_in, rows, cols, sizeof(float),
+                          exclusive != 0, ws, ws_bytes, variant, stream);
+}
+
+gbscan_status scan_backward_f64(const double* grad_out, double* grad_in, int64_t rows,
+                                int64_t cols, int exclusive, void* ws, size_t ws_bytes,
+                                int variant, cudaStream_t stream) {
+    return scan_rows_impl(family_rows_rev_f64(), grad_out, grad_in, rows, cols, sizeof(double),
+                          exclusive != 0, ws, ws_bytes, variant, stream);
+}
+
+gbscan_status scan_get_device_status(void* ws, cudaStream_t stream) {
+    if (ws == nullptr) return GBSCAN_ERR_WORKSPACE;
+    Header* hdr = static_cast<Header*>(ws);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return GBSCAN_ERR_CUDA;
+    int32_t err = 0;
+    if (cudaMemcpy(&err, &hdr->error, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GBSCAN_ERR_CUDA;
+    if (err != 0) {
+        if (cudaMemsetAsync(&hdr->error, 0, sizeof(int32_t), stream) != cudaSuccess)
+            return GBSCAN_ERR_CUDA;
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return GBSCAN_ERR_CUDA;
+    }
+    return static_cast<gbscan_status>(err);
+}
+
+gbscan_status gbscan_set_debug(void* ws, size_t ws_bytes, uint32_t spin_limit_us,
+                               int64_t drop_tile, uint32_t delay_ns_max, cudaStream_t stream) {
+    if (ws == nullptr || ws_bytes < kHeaderBytes) return GBSCAN_ERR_WORKSPACE;
+    cudaGetLastError();
+    set_debug_kernel<<<1, 1, 0, stream>>>(static_cast<Header*>(ws), spin_limit_us, drop_tile,
+                                          delay_ns_max);
+    return from_cuda(cudaGetLastError());
+}
+
+int gbscan_num_variants(gbscan_dtype dtype, gbscan_kind kind) {
+    if (!valid_dtype(dtype)) return 0;
+    const Family* f = family_for(dtype, kind);
+    return f ? f->num_variants : 0;
+}
+
+gbscan_status gbscan_variant_info(gbscan_dtype dtype, gbscan_kind kind, int variant, int* threads,
+                                  int* items, int* stages, int* tile) {
+    if (!valid_dtype(dtype)) return GBSCAN_ERR_INVALID_ARG;
+    const Family* f = family_for(dtype, kind);
+    if (!f) return GBSCAN_ERR_UNSUPPORTED;
+    if (variant < 0 || variant >= f->num_variants) return GBSCAN_ERR_INVALID_ARG;
+    const Variant& v = f->variants[variant];
+    if (threads) *threads = v.threads;
+    if (items) *items = v.items;
+    if (stages) *stages = v.stages;
+    if (tile) *tile = v.tile;
+    return GBSCAN_OK;
+}
+
+gbscan_status gbscan_copy(const void* src, void* dst, size_t bytes, cudaStream_t stream) {
+    if (bytes == 0) return GBSCAN_OK;
+    if (src == nullptr || dst == nullptr) return GBSCAN_ERR_INVALID_ARG;
+    if (ranges_overlap(src, bytes, dst, bytes)) return GBSCAN_ERR_INVALID_ARG;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) || (bytes & 15))
+        return GBSCAN_ERR_ALIGNMENT;
+    cudaGetLastError();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = device_sm_count(dev);
+    const int64_t n16 = static_cast<int64_t>(bytes / 16);
+    int64_t blocks = static_cast<int64_t>(sms > 0 ? sms : 1) * 8;
+    const int64_t need = (n16 + 255) / 256;
+    if (blocks > need) blocks = need;
+    copy_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
+        static_cast<const uint4*>(src), static_cast<uint4*>(dst), n16);
+    return from_cuda(cudaGetLastError());
+}
+
+const char* gbscan_status_string(gbscan_status status) {
+    switch (status) {
+    case GBSCAN_OK: return "ok";
+    case GBSCAN_ERR_INVALID_ARG: return "invalid argument";
+    case GBSCAN_ERR_ALIGNMENT: return "misaligned pointer";
+    case GBSCAN_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case GBSCAN_ERR_CUDA: return "CUDA error";
+    case GBSCAN_ERR_TIMEOUT: return "bounded wait on another tile ran out";
+    case GBSCAN_ERR_UNSUPPORTED: return "unsupported size or option";
+    }
+    return "unknown status";
+}
+
+int gbscan_abi_version(void) { return GBSCAN_ABI_VERSION; }
+
+}  // extern "C"

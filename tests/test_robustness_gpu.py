@@ -1,0 +1,165 @@
+"""Ordering stress, bounded waits, CUDA-graph replay and autograd on the GPU.
+
+No test here faults or hangs the GPU: the "dropped tile" case makes one tile
+skip its status publication, and its successor's bounded wait (a 2 ms limit
+set in the workspace header) runs out and records GBSCAN_ERR_TIMEOUT, which
+the host reads back; the kernel finishes normally.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2312_14874_gb300 as gb
+from paper_2312_14874_gb300 import _capi
+from paper_2312_14874_gb300.graphs import SegmentedScanGraph
+
+pytestmark = pytest.mark.gpu
+
+
+def dev():
+    return torch.device("cuda", 0)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def test_race_stress_random_publication_delays():
+    """Pseudo-random sleeps before every status publication reorder tile
+    completion; integer results must stay bit-exact over many repetitions,
+    with far more tiles than resident blocks."""
+    n = 600 * 5120 + 333
+    a = synth.uniform_i32(n, 1 << 16, seed=1)
+    want = oracle.scan_i32(a)
+    x = to_dev(a)
+    ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_SCAN, n))
+    gb.set_debug(delay_ns_max=3000, workspace=ws)
+    for rep in range(30):
+        v = rep % gb.num_variants(torch.int32)
+        y = gb.inclusive(x, variant=v, workspace=ws).cpu().numpy()
+        assert np.array_equal(y, want), rep
+    gb.set_debug(workspace=ws)
+    assert gb.device_status(ws) == 0
+
+
+def test_race_stress_segmented_and_i64():
+    off = synth.segment_offsets(3000, max_log2=12, seed=2)
+    n = int(off[-1])
+    a = synth.uniform_i32(n, 4, seed=3)
+    ws = gb.Workspace(gb.workspace_bytes(torch.int64, _capi.KIND_SCAN, n))
+    gb.set_debug(delay_ns_max=2000, workspace=ws)
+    x, o = to_dev(a), to_dev(off)
+    want = oracle.seg_scan_i32(a, off, True)
+    b = synth.uniform_i64(n, 1 << 32, seed=4)
+    want64 = oracle.scan_i64(b)
+    xb = to_dev(b)
+    for rep in range(10):
+        assert np.array_equal(gb.segmented(x, o, exclusive=True, workspace=ws).cpu().numpy(), want)
+        assert np.array_equal(gb.inclusive(xb, workspace=ws).cpu().numpy(), want64)
+    gb.set_debug(workspace=ws)
+    assert gb.device_status(ws) == 0
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64, torch.float32])
+def test_dropped_tile_times_out_and_recovers(dtype):
+    n = 50 * 5120
+    ws = gb.Workspace(gb.workspace_bytes(dtype, _capi.KIND_SCAN, n))
+    x = torch.ones(n, dtype=dtype, device=dev())
+    gb.set_debug(spin_limit_us=2000, drop_tile=17, workspace=ws)
+    gb.inclusive(x, workspace=ws)
+    assert gb.device_status(ws) == _capi.ERR_TIMEOUT
+    assert gb.device_status(ws) == 0  # cleared by the read
+    # the workspace is usable again once the hook is removed
+    gb.set_debug(workspace=ws)
+    y = gb.inclusive(x, workspace=ws)
+    assert torch.equal(y.long(), torch.arange(1, n + 1, device=dev()))
+    assert gb.device_status(ws) == 0
+
+
+def test_cuda_graph_segmented_replay():
+    """Capture the segmented scan once, then replay it on new data written into
+    the same input buffer; the epoch kept on the device makes each replay
+    start from clean status words."""
+    off = synth.segment_offsets(2000, max_log2=14, seed=7)
+    n = int(off[-1])
+    g = SegmentedScanGraph(n, off, torch.int32, exclusive=True)
+    for rep in range(10):
+        a = synth.uniform_i32(n, 4, seed=50 + rep)
+        y = g.run(torch.from_numpy(a).to(dev())).cpu().numpy()
+        assert np.array_equal(y, oracle.seg_scan_i32(a, off, True)), rep
+    assert g.device_status() == 0
+
+
+def test_cuda_graph_plain_scan_replay():
+    n = (1 << 20) + 5
+    x = torch.empty(n, dtype=torch.float32, device=dev())
+    y = torch.empty_like(x)
+    ws = gb.Workspace(gb.workspace_bytes(torch.float32, _capi.KIND_SCAN, n))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        gb.inclusive(x.zero_(), out=y, workspace=ws, compensated=True)  # warm-up (lazy init)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gb.inclusive(x, out=y, workspace=ws, compensated=True)
+    for rep in range(10):
+        a = synth.normal_f32(n, seed=rep)
+        x.copy_(torch.from_numpy(a))
+        graph.replay()
+        torch.cuda.synchronize()
+        err, _ = oracle.max_rel_err(y.cpu().numpy(), oracle.scan_f32_ref(a), oracle.abs_scan_f32(a))
+        assert err <= 1e-6
+
+
+# ---- autograd -------------------------------------------------------------------
+
+def test_gradcheck_fp64():
+    x = torch.randn(8, 64, dtype=torch.float64, device=dev(), requires_grad=True)
+    for excl in (False, True):
+        assert torch.autograd.gradcheck(lambda t: gb.cumsum(t, -1, excl), (x,), eps=1e-6,
+                                        atol=1e-9, rtol=1e-7)
+    y = torch.randn(6, 5, 7, dtype=torch.float64, device=dev(), requires_grad=True)
+    assert torch.autograd.gradcheck(lambda t: gb.cumsum(t, 1), (y,))
+
+
+def test_finite_differences_fp32():
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn(4, 300, generator=g).to(dev())
+    w = torch.randn(4, 300, generator=g).to(dev())
+    xr = x.clone().requires_grad_(True)
+    (gb.cumsum(xr) * w).sum().backward()
+    h = 1e-2
+    for (r, c) in [(0, 0), (1, 17), (2, 150), (3, 299)]:
+        xp, xm = x.clone(), x.clone()
+        xp[r, c] += h
+        xm[r, c] -= h
+        fd = ((gb.cumsum(xp) * w).sum() - (gb.cumsum(xm) * w).sum()).item() / (2 * h)
+        assert abs(fd - xr.grad[r, c].item()) <= 1e-3 * max(1.0, abs(fd)) + 2e-2
+
+
+def test_backward_matches_oracle_and_forward_matches_cumsum():
+    rows, cols = 64, 3000
+    a = synth.normal_f32(rows * cols, seed=8).reshape(rows, cols)
+    gnp = synth.normal_f32(rows * cols, seed=9).reshape(rows, cols)
+    x = to_dev(a).requires_grad_(True)
+    y = gb.cumsum(x, -1)
+    y.backward(to_dev(gnp))
+    off = np.arange(rows + 1, dtype=np.int64) * cols
+    err, _ = oracle.max_rel_err(y.detach().cpu().numpy(),
+                                oracle.seg_scan_f32_ref(a.reshape(-1), off).reshape(rows, cols),
+                                oracle.seg_abs_scan_f32(a.reshape(-1), off).reshape(rows, cols))
+    assert err <= 1e-5
+    err, _ = oracle.max_rel_err(x.grad.cpu().numpy(), oracle.rows_suffix_f32_ref(gnp),
+                                oracle.rows_suffix_abs_f32(gnp))
+    assert err <= 1e-5
+    # dim != -1 goes through a transpose
+    x2 = to_dev(a).requires_grad_(True)
+    y2 = gb.cumsum(x2, 0)
+    y2.backward(to_dev(gnp))
+    ref = oracle.rows_suffix_f32_ref(np.ascontiguousarray(gnp.T)).T
+    err, _ = oracle.max_rel_err(x2.grad.cpu().numpy(), ref,
+                                oracle.rows_suffix_abs_f32(np.ascontiguousarray(gnp.T)).T)
+    assert err <= 1e-5
