@@ -1,0 +1,494 @@
+"""Benchmark: inclusive prefix sum of int32, n = 2^30, values uniform in
+[0, 255] (seed 0), single-pass chained scan on one GB300.
+
+One step = one pass of the whole scan (tile load, register/warp/block scan,
+look-back, carry add, store) over the 2^30-element array, one kernel launch.
+The metric is GB/s = (bytes read + bytes written) / device time, with
+8 * 2^30 bytes per step; inputs (4 GiB) and outputs are larger than the
+129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Extra fields: the roofline of the scan kernel
+against the measured HBM copy bandwidth, the end-to-end number through the
+public API with host buffers, SM clocks sampled during the timed region, the
+CPU oracle timed on a bounded sample (cpu_baseline), and side measurements of
+the other kernels (two-pass, int64, fp32 plain/compensated, segmented,
+row-wise forward/backward, device copy) at their own sizes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica on its own GPU (the
+scan does not shard here: replicas only); value = bytes of all ranks / the
+slowest rank's time.  ``--impl reference`` times the CPU oracle on the host
+cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_LOG2 = 30
+N = 1 << N_LOG2
+VALUE_RANGE = 256  # uniform integers in [0, 255]
+BYTES_PER_STEP = 2 * 4 * N  # int32 read + write
+METRIC = "scan GB/s (read+write bytes/device time) and % of HBM roofline; fp32 max rel err"
+WORKLOAD = "int32 inclusive scan, n=2^30, uniform [0,255], seed 0, single-pass decoupled look-back"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-side", action="store_true", help="skip the side measurements")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--n-log2", type=int, default=N_LOG2,
+                    help="array size 2^k (profiling runs use a smaller case; the benchmark "
+                         "workload is 2^30)")
+    return ap.parse_args(argv)
+
+
+# ---- distributed helpers (also used by the CPU tests with gloo) -------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Maximum of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(bytes_per_rank: float, seconds_max: float, world: int) -> float:
+    """Whole-job GB/s: the bytes every rank moved over the slowest rank's time."""
+    return bytes_per_rank * world / seconds_max / 1e9
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---- clocks ------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.5)
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ---- peaks -------------------------------------------------------------------
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def cuda_time_ms(fn, reps: int, flush=None) -> tuple[float, float]:
+    """(median, min) ms of fn over reps, CUDA events on the current stream;
+    flush() runs between reps outside the timed interval."""
+    import torch
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times), min(times)
+
+
+# ---- CPU oracle baseline ------------------------------------------------------
+
+def cpu_oracle_baseline(h_in_np, budget_s: float = 10.0) -> dict:
+    """The oracle's sequential scan (single host thread) on the same input:
+    whole passes over the 2^30-element array until about budget_s seconds."""
+    import numpy as np
+    import oracle
+    a = h_in_np
+    out = np.empty_like(a)
+    lib = oracle._load()
+    reps, t_total = 0, 0.0
+    while t_total < budget_s and reps < 20:
+        t0 = time.perf_counter()
+        lib.oracle_scan_i32(a.ctypes.data, out.ctypes.data, a.size, 0)
+        t_total += time.perf_counter() - t0
+        reps += 1
+    secs = t_total / reps
+    return {"value": round(2 * 4 * a.size / secs / 1e9, 3), "unit": "GB/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{reps} full passes of the sequential oracle over the same 2^{N_LOG2} "
+                      f"int32 input on one host thread ({secs * 1e3:.0f} ms per pass)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed on the host cores."""
+    import numpy as np
+    import oracle
+    import synth
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    sample_log2 = 26  # each step: a 2^26-element prefix of the 2^30 workload
+    m = 1 << sample_log2
+    a = np.empty(m, dtype=np.int32)
+    synth.uniform_i32_into(a.ctypes.data, m, VALUE_RANGE, seed=0)
+    out = np.empty_like(a)
+    lib = oracle._load()
+    for _ in range(args.warmup):
+        lib.oracle_scan_i32(a.ctypes.data, out.ctypes.data, m, 0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        lib.oracle_scan_i32(a.ctypes.data, out.ctypes.data, m, 0)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = 2 * 4 * m * args.steps / total / 1e9
+    sample = (f"each step scans the first 2^{sample_log2} elements of the 2^{N_LOG2} int32 "
+              f"workload with the sequential CPU oracle on one host thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "sample_n": m},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- side measurements ----------------------------------------------------------
+
+def side_measurements(dev, peak) -> dict:
+    """Each other kernel at its own configuration, CUDA-event timed (median of
+    reps).  Inputs > L2 except the [4096, 8192] row tensors (128 MiB), which
+    are timed with an L2 flush (a 512 MiB write) between reps."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2312_14874_gb300 as gb
+    from paper_2312_14874_gb300 import _capi
+    from paper_2312_14874_gb300.graphs import SegmentedScanGraph
+
+    res = {}
+
+    def rec(name, nbytes, ms):
+        res[name] = {"gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "ms": round(ms, 4),
+                     "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak, 3)}
+
+    reps = 20
+    # int32 2^30 variants of the headline: exclusive, two-pass, copy references
+    x = torch.empty(N, dtype=torch.int32, device=dev)
+    x.random_(0, VALUE_RANGE)
+    y = torch.empty_like(x)
+    ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_SCAN, N), dev)
+    rec("i32_2^30_exclusive", 8 * N, cuda_time_ms(lambda: gb.exclusive(x, out=y, workspace=ws), reps)[0])
+    rec("i32_2^30_two_pass", 8 * N, cuda_time_ms(
+        lambda: gb.inclusive(x, out=y, workspace=ws, algo="two_pass"), reps)[0])
+    rec("copy_torch_4GiB", 8 * N, cuda_time_ms(lambda: y.copy_(x), reps)[0])
+    rec("copy_gbscan_4GiB", 8 * N, cuda_time_ms(lambda: gb.copy_(y, x), reps)[0])
+    for v in range(gb.num_variants(torch.int32)):
+        rec(f"i32_2^30_variant{v}", 8 * N, cuda_time_ms(
+            lambda: gb.inclusive(x, out=y, workspace=ws, variant=v), reps)[0])
+    del x, y
+    # int64 2^29
+    n64 = 1 << 29
+    x = torch.empty(n64, dtype=torch.int64, device=dev).random_(0, 1 << 32)
+    y = torch.empty_like(x)
+    rec("i64_2^29_single_pass", 16 * n64, cuda_time_ms(lambda: gb.inclusive(x, out=y, workspace=ws), reps)[0])
+    rec("i64_2^29_two_pass", 16 * n64, cuda_time_ms(
+        lambda: gb.inclusive(x, out=y, workspace=ws, algo="two_pass"), reps)[0])
+    del x, y
+    # fp32 2^28, plain and compensated
+    nf = 1 << 28
+    x = torch.randn(nf, device=dev)
+    y = torch.empty_like(x)
+    rec("f32_2^28_plain", 8 * nf, cuda_time_ms(lambda: gb.inclusive(x, out=y, workspace=ws), reps)[0])
+    rec("f32_2^28_compensated", 8 * nf, cuda_time_ms(
+        lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True), reps)[0])
+    del x, y
+    # segmented: 65,536 log-uniform segments in [1, 2^16], exclusive, CUDA graph
+    off = synth.segment_offsets(65536, max_log2=16, seed=0)
+    ns = int(off[-1])
+    for dt in (torch.int32, torch.float32):
+        g = SegmentedScanGraph(ns, off, dt, exclusive=True, device=dev)
+        if dt == torch.int32:
+            g.x.random_(0, 4)
+        else:
+            g.x.uniform_()
+        rec(f"seg_{'i32' if dt == torch.int32 else 'f32'}_65536segs_exclusive_graph",
+            8 * ns + 8 * (off.size), cuda_time_ms(g.replay, reps)[0])
+        del g
+    res["seg_total_n"] = ns
+    # rows [4096, 8192] fp32: forward and backward, L2 flushed between reps
+    rows, cols = 4096, 8192
+    xr = torch.randn(rows, cols, device=dev)
+    yr = torch.empty_like(xr)
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush = lambda: flush_buf.fill_(1)
+    rec("rows_f32_4096x8192_forward", 8 * rows * cols, cuda_time_ms(
+        lambda: gb.rows(xr, out=yr, workspace=ws), reps, flush)[0])
+    rec("rows_f32_4096x8192_backward", 8 * rows * cols, cuda_time_ms(
+        lambda: gb.backward(xr, out=yr, workspace=ws), reps, flush)[0])
+    rec("plain_f32_2^25_flushed", 8 * rows * cols, cuda_time_ms(
+        lambda: gb.inclusive(xr.view(-1), out=yr.view(-1), workspace=ws), reps, flush)[0])
+    del xr, yr, flush_buf
+    return res
+
+
+# ---- main ------------------------------------------------------------------------
+
+def main(argv=None) -> int:
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_2312_14874_gb300 as gb
+    from paper_2312_14874_gb300 import _capi, autotune
+
+    global N, BYTES_PER_STEP, WORKLOAD
+    if args.n_log2 != N_LOG2:
+        N = 1 << args.n_log2
+        BYTES_PER_STEP = 2 * 4 * N
+        WORKLOAD = WORKLOAD.replace(f"n=2^{N_LOG2}", f"n=2^{args.n_log2}")
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    peak, peak_kind = measured_hbm_peak()
+
+    # host input in pinned memory (also the source of the e2e copies)
+    h_in = torch.empty(N, dtype=torch.int32, pin_memory=True)
+    synth.uniform_i32_into(h_in.data_ptr(), N, VALUE_RANGE, seed=0)
+    x = h_in.to(dev)
+    y = torch.empty_like(x)
+    ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_SCAN, N), dev)
+    variant = autotune.choose("scan_i32", "i32", N)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        gb.inclusive(x, out=y, workspace=ws, variant=variant)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    # sanity: the last prefix is the total (mod 2^32)
+    total = int(x.sum(dtype=torch.int64).item()) % (1 << 32)
+    last = int(y[-1].item()) % (1 << 32)
+    if total != last:
+        raise RuntimeError("scan result failed the last == total check")
+
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(dev)
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dev)
+    clk = clocks.stop()
+    total_ms = starts[0].elapsed_time(ends[-1])
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    avg_launch_ms = sum(launch_ms) / len(launch_ms)
+    secs_max = max_over_ranks(total_ms / 1e3, dev)
+    value = aggregate(BYTES_PER_STEP * args.steps, secs_max, world)
+    ms_per_step = secs_max * 1e3 / args.steps
+    achieved = BYTES_PER_STEP / (avg_launch_ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host input -> device -> scan ->
+    # pinned host output, every step
+    e2e = None
+    if not args.no_e2e:
+        h_out = torch.empty(N, dtype=torch.int32, pin_memory=True)
+        e2e_steps = 3
+
+        def e2e_step():
+            x.copy_(h_in, non_blocking=True)
+            gb.inclusive(x, out=y, workspace=ws, variant=variant)
+            h_out.copy_(y, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_secs = max_over_ranks(a.elapsed_time(b) / 1e3 / e2e_steps, dev)
+        e2e = {"value": round(aggregate(BYTES_PER_STEP, e2e_secs, world), 3), "unit": "GB/s",
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
+               "ms_per_step": round(e2e_secs * 1e3, 3)}
+        del h_out
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and args.n_log2 == N_LOG2:
+        cpu = cpu_oracle_baseline(h_in.numpy())
+
+    side = None
+    if rank == 0 and not args.no_side and args.n_log2 == N_LOG2:
+        del y
+        torch.cuda.empty_cache()
+        side = side_measurements(dev, peak)
+
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(prof) as f:
+            tj = json.load(f)
+        if tj.get("kernel_variant") == variant and tj.get("source_stamp") == _source_stamp():
+            traffic = tj.get("bytes_per_launch_full")
+    except (OSError, ValueError):
+        pass
+
+    if rank == 0:
+        vinfo = gb.variant_info(torch.int32, _capi.KIND_SCAN, variant)
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "dtype": "int32", "values": "uniform [0,255]",
+                       "algo": "single_pass", "variant": variant, **vinfo,
+                       "l2": "inputs and outputs 4 GiB each, larger than the 129 MB L2: no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)",
+                         "bytes_per_launch": BYTES_PER_STEP,
+                         "avg_launch_ms": round(avg_launch_ms, 4)},
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                       "reasons": clk["reasons"], "samples": clk["samples"],
+                       "power_w_max": clk.get("power_w_max")},
+            "cpu_baseline": cpu,
+            "side": side,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _source_stamp() -> str:
+    """Hash of the kernel sources, to tell whether a recorded ncu traffic
+    figure still describes the current kernel."""
+    import hashlib
+    import glob
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2312_14874_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

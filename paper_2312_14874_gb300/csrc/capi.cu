@@ -21,11 +21,11 @@ int device_sm_count(int device) {
     return sms;
 }
 
-// rec[t].aux = first segment whose start is >= t * tile (lower bound over the
+// aux[t] = first segment whose start is >= t * tile (lower bound over the
 // offsets), for t = 0..num_tiles; the tile kernel marks the starts of
-// segments [rec[t].aux, rec[t+1].aux) as heads.  Also checks the CSR offsets.
+// segments [aux[t], aux[t+1]) as heads.  Also checks the CSR offsets.
 __global__ void segment_locate_kernel(const int64_t* offsets, int64_t num_segments, int64_t n,
-                                      int64_t tile, int64_t num_tiles, TileRecord* rec,
+                                      int64_t tile, int64_t num_tiles, unsigned long long* rec,
                                       Header* hdr) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -40,7 +40,7 @@ __global__ void segment_locate_kernel(const int64_t* offsets, int64_t num_segmen
             else
                 hi = mid;
         }
-        rec[t].aux = static_cast<unsigned long long>(lo);
+        *rec_aux(rec, t) = static_cast<unsigned long long>(lo);
     }
     bool bad = false;
     for (int64_t j = first; j < num_segments; j += stride)
@@ -83,15 +83,17 @@ int min_tile(gbscan_dtype dt) {
 bool valid_dtype(int dt) { return dt >= GBSCAN_I32 && dt <= GBSCAN_F64; }
 
 // Records needed for n elements at tile size `tile`: one per tile plus the
-// segment locator's end sentinel.
+// segment locator's end sentinel; they come in blocks of 16.
 int64_t records_for(int64_t n, int tile) { return (n + tile - 1) / tile + 1; }
+
+size_t record_bytes(int64_t records) {
+    return static_cast<size_t>((records + 15) / 16) * kRecBlockBytes;
+}
 
 gbscan_status check_ws(void* ws, size_t ws_bytes, int64_t records) {
     if (ws == nullptr) return GBSCAN_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return GBSCAN_ERR_WORKSPACE;
-    if (ws_bytes < kHeaderBytes) return GBSCAN_ERR_WORKSPACE;
-    const uint64_t cap = (ws_bytes - kHeaderBytes) / sizeof(TileRecord);
-    if (static_cast<uint64_t>(records) > cap) return GBSCAN_ERR_WORKSPACE;
+    if (ws_bytes < kHeaderBytes + record_bytes(records)) return GBSCAN_ERR_WORKSPACE;
     return GBSCAN_OK;
 }
 
@@ -120,8 +122,8 @@ Params make_params(const void* in, void* out, int64_t n, int tile, void* ws, siz
     p.n = n;
     p.num_tiles = (n + tile - 1) / tile;
     p.hdr = static_cast<Header*>(ws);
-    p.rec = reinterpret_cast<TileRecord*>(static_cast<unsigned char*>(ws) + kHeaderBytes);
-    p.rec_capacity = static_cast<int64_t>((ws_bytes - kHeaderBytes) / sizeof(TileRecord));
+    p.rec = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(ws) + kHeaderBytes);
+    p.rec_capacity = static_cast<int64_t>((ws_bytes - kHeaderBytes) / kRecBlockBytes) * 16;
     p.fast = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     return p;
 }
@@ -246,7 +248,7 @@ gbscan_status gbscan_workspace_size(gbscan_dtype dtype, gbscan_kind kind, int64_
     if (num_segments > INT32_MAX) return GBSCAN_ERR_UNSUPPORTED;
     const int tile = min_tile(dtype);
     if ((n + tile - 1) / tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
-    *bytes = kHeaderBytes + static_cast<size_t>(records_for(n, tile)) * sizeof(TileRecord);
+    *bytes = kHeaderBytes + record_bytes(records_for(n, tile));
     return GBSCAN_OK;
 }
 

@@ -55,27 +55,49 @@ struct alignas(256) Header {
     uint32_t spin_limit_us; // bound on every wait, 0 = default
     uint32_t delay_ns_max;  // race-stress sleeps before publishing, 0 = off
     int64_t drop_tile_plus1;// debug: this tile (minus one) never publishes, 0 = none
-    uint32_t reserved[54];
+    uint32_t abort_epoch;   // epoch of a launch in which a bounded wait ran out
+    uint32_t reserved[53];
 };
 static_assert(sizeof(Header) == 256, "header size");
 
-// One record per tile.  The status word of tile i lives only in `word` of record
-// i, whatever the element type, kind or size of the call, so a later call can
-// never read a value written by another layout as a status word.
-//   word : bits 0..31  tile value (4-byte accumulators: aggregate or inclusive prefix)
-//          bits 32..33 state (0 = not ready, 1 = aggregate, 2 = inclusive prefix)
-//          bit  34     the tile contains a segment head
-//          bits 35..63 epoch of the launch that wrote it
-//   agg, inc : 8-byte accumulators (aggregate / inclusive prefix), written before
-//          the word is released.
-//   aux  : two-pass tile sums, or the first segment of the tile.
-struct alignas(32) TileRecord {
-    unsigned long long word;
-    unsigned long long agg;
-    unsigned long long inc;
-    unsigned long long aux;
-};
-static_assert(sizeof(TileRecord) == 32, "record size");
+// Tile records, 16 tiles to a 512-byte block:
+//   block b = tile / 16 (also the tile's group), slot = tile % 16
+//   lo[16]  words  0..15 : status word of each tile
+//   hi[16]  words 16..31 : 8-byte accumulators only: second status word
+//   aux[16] words 32..47 : two-pass tile sums, or the first segment of the tile
+//   glo, ghi words 48, 49 : status words of the group (the block's 16 tiles)
+//   words 50..63          : unused
+// A status word holds
+//   bits 0..31  the value (4-byte accumulators), or one 32-bit half of an
+//               8-byte accumulator (lo: bits 0..31, hi: bits 32..63)
+//   bits 32..33 state (0 = not ready, 1 = aggregate, 2 = inclusive prefix)
+//   bit  34     the tile (or group) contains a segment head
+//   bits 35..63 epoch of the launch that wrote it
+// For 8-byte accumulators a reader takes the pair only when both words carry
+// the same bits 32..63, which identifies one publication (each state is
+// published once per launch).  Status words live only in lo/hi/glo/ghi,
+// whatever the element type, kind or size of a call, and nothing else is
+// written there, so no call can read another call's data as a status word.
+// Sixteen tile status words share one 128-byte line.
+constexpr int kGroup = 16;                 // tiles per group (and per block)
+constexpr int kRecBlockWords = 64;         // u64 words per block
+constexpr int kRecBlockBytes = kRecBlockWords * 8;
+
+__device__ __forceinline__ unsigned long long* rec_lo(unsigned long long* rec, int64_t t) {
+    return rec + (t >> 4) * kRecBlockWords + (t & 15);
+}
+__device__ __forceinline__ unsigned long long* rec_hi(unsigned long long* rec, int64_t t) {
+    return rec + (t >> 4) * kRecBlockWords + 16 + (t & 15);
+}
+__device__ __forceinline__ unsigned long long* rec_aux(unsigned long long* rec, int64_t t) {
+    return rec + (t >> 4) * kRecBlockWords + 32 + (t & 15);
+}
+__device__ __forceinline__ unsigned long long* rec_glo(unsigned long long* rec, int64_t g) {
+    return rec + g * kRecBlockWords + 48;
+}
+__device__ __forceinline__ unsigned long long* rec_ghi(unsigned long long* rec, int64_t g) {
+    return rec + g * kRecBlockWords + 49;
+}
 
 constexpr uint32_t kStateX = 0, kStateA = 1, kStateP = 2;
 constexpr uint32_t kEpochBits = 29;
@@ -91,8 +113,8 @@ struct Params {
     int64_t n;
     int64_t num_tiles;
     Header* hdr;
-    TileRecord* rec;
-    int64_t rec_capacity;   // records the workspace holds
+    unsigned long long* rec; // tile records (blocks of 16, see above)
+    int64_t rec_capacity;    // tiles the workspace holds records for
     const int64_t* offsets; // segmented: CSR offsets (num_segments + 1)
     int64_t num_segments;
     int64_t cols;           // row kinds: row length
@@ -131,6 +153,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// As mbar_try_wait, but the thread may be suspended in hardware for up to
+// `hint_ns` while the phase is incomplete; it resumes as soon as the phase
+// completes.  Waiting threads then do not keep the shared-memory pipe busy.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
@@ -188,6 +226,23 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
+// Status-word poll: a plain 64-bit load served by L2, the point of coherence
+// (.cg: not cached in L1, so every poll sees the latest value L2 holds).
+// Unlike a .relaxed/.acquire load, consecutive .cg loads of one thread are
+// pipelined, so a lane can read several status words in one round trip.  An
+// aligned 8-byte word is read whole; a word that is stale or not yet written
+// fails the epoch check and is read again on the next poll, and every poll
+// round ends with a fence so that no re-read can be merged away.
+__device__ __forceinline__ unsigned long long ld_poll_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void poll_round_fence() {
+    asm volatile("fence.acq_rel.cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -204,6 +259,25 @@ __device__ __forceinline__ int32_t ld_relaxed_s32(const int32_t* p) {
 
 __device__ __forceinline__ void record_error(Header* hdr, int code, int64_t tile) {
     if (atomicCAS(&hdr->error, 0, code) == 0) hdr->error_tile = tile;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// A bounded wait ran out in the launch tagged `epoch`: record the error (kept
+// until scan_get_device_status reads it) and mark the launch aborted, so that
+// its other waits give up at once instead of each running into the bound.
+// The mark names the launch, so later launches are not affected.
+__device__ __forceinline__ void record_timeout(Header* hdr, uint32_t epoch, int64_t tile) {
+    record_error(hdr, GBSCAN_ERR_TIMEOUT, tile);
+    atomicExch(&hdr->abort_epoch, epoch);
+}
+
+__device__ __forceinline__ bool launch_aborted(const Header* hdr, uint32_t epoch) {
+    return ld_relaxed_u32(&hdr->abort_epoch) == epoch;
 }
 
 // ---------------------------------------------------------------------------
@@ -353,34 +427,36 @@ __device__ __forceinline__ uint32_t make_meta(uint32_t epoch, bool head, uint32_
     return (epoch << 3) | (head ? 4u : 0u) | state;
 }
 
+// Publishes (state, head, v) into a status word pair (hi unused for 4-byte
+// accumulators).
 template <class Op>
-__device__ __forceinline__ void publish(TileRecord* rec, int64_t tile, uint32_t epoch,
-                                        uint32_t state, bool head, typename Op::Acc v) {
-    TileRecord* r = rec + tile;
-    const unsigned long long meta = make_meta(epoch, head, state);
+__device__ __forceinline__ void publish_words(unsigned long long* lo, unsigned long long* hi,
+                                              uint32_t epoch, uint32_t state, bool head,
+                                              typename Op::Acc v) {
+    const unsigned long long meta = static_cast<unsigned long long>(make_meta(epoch, head, state)) << 32;
+    const unsigned long long bits = static_cast<unsigned long long>(Op::to_bits(v));
     if constexpr (Op::kPacked) {
-        st_relaxed_u64(&r->word, (meta << 32) | static_cast<unsigned long long>(Op::to_bits(v)));
+        st_relaxed_u64(lo, meta | bits);
     } else {
-        // Value first, then the status word with release order, so that a
-        // reader that acquires the word sees the value.  Aggregate and prefix
-        // have separate slots: a reader that saw state A never reads a prefix.
-        st_relaxed_u64(state == kStateP ? &r->inc : &r->agg,
-                       static_cast<unsigned long long>(Op::to_bits(v)));
-        st_release_u64(&r->word, meta << 32);
+        // 8-byte values: each half travels in its own 64-bit word together with
+        // the same status meta; a reader accepts the pair only when both metas
+        // agree, which identifies one publication (one state per launch).
+        st_relaxed_u64(lo, meta | (bits & 0xffffffffull));
+        st_relaxed_u64(hi, meta | (bits >> 32));
     }
 }
 
 template <class Op>
-__device__ __forceinline__ void read_status(const TileRecord* rec, int64_t tile, uint32_t epoch,
-                                            uint32_t& state, bool& head, typename Op::Acc& v) {
-    const TileRecord* r = rec + tile;
-    unsigned long long w;
-    if constexpr (Op::kPacked)
-        w = ld_relaxed_u64(&r->word);
-    else
-        w = ld_acquire_u64(&r->word);
-    const uint32_t meta = static_cast<uint32_t>(w >> 32);
-    if ((meta >> 3) != epoch) {
+__device__ __forceinline__ void read_words(const unsigned long long* lo, const unsigned long long* hi,
+                                           uint32_t epoch, uint32_t& state, bool& head,
+                                           typename Op::Acc& v) {
+    const unsigned long long w0 = ld_poll_u64(lo);
+    unsigned long long w1 = 0;
+    if constexpr (!Op::kPacked) w1 = ld_poll_u64(hi);
+    const uint32_t meta = static_cast<uint32_t>(w0 >> 32);
+    bool ok = (meta >> 3) == epoch;
+    if constexpr (!Op::kPacked) ok = ok && static_cast<uint32_t>(w1 >> 32) == meta;
+    if (!ok) {
         state = kStateX;
         head = false;
         v = Op::identity();
@@ -388,12 +464,22 @@ __device__ __forceinline__ void read_status(const TileRecord* rec, int64_t tile,
     }
     state = meta & 3u;
     head = (meta & 4u) != 0;
-    if constexpr (Op::kPacked) {
-        v = Op::from_bits(static_cast<typename Op::Bits>(w & 0xffffffffull));
-    } else {
-        v = Op::from_bits(static_cast<typename Op::Bits>(
-            ld_relaxed_u64(state == kStateP ? &r->inc : &r->agg)));
-    }
+    if constexpr (Op::kPacked)
+        v = Op::from_bits(static_cast<typename Op::Bits>(w0 & 0xffffffffull));
+    else
+        v = Op::from_bits(static_cast<typename Op::Bits>((w1 << 32) | (w0 & 0xffffffffull)));
+}
+
+template <class Op>
+__device__ __forceinline__ void publish(unsigned long long* rec, int64_t tile, uint32_t epoch,
+                                        uint32_t state, bool head, typename Op::Acc v) {
+    publish_words<Op>(rec_lo(rec, tile), rec_hi(rec, tile), epoch, state, head, v);
+}
+
+template <class Op>
+__device__ __forceinline__ void publish_group(unsigned long long* rec, int64_t g, uint32_t epoch,
+                                              uint32_t state, bool head, typename Op::Acc v) {
+    publish_words<Op>(rec_glo(rec, g), rec_ghi(rec, g), epoch, state, head, v);
 }
 
 __device__ __forceinline__ uint32_t mix32(uint64_t x) {
@@ -404,549 +490,265 @@ __device__ __forceinline__ uint32_t mix32(uint64_t x) {
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory control block of the tile kernel
+// Decoupled look-back (all 32 lanes of one warp)
 // ---------------------------------------------------------------------------
 
-template <class Op, int STAGES, int NWARPS, int TILE>
-struct Ctrl {
-    using Acc = typename Op::Acc;
-    uint64_t mbar[STAGES];
-    int64_t tile_id[STAGES];
-    Acc wtot_v[NWARPS];
-    Acc tex_v;  // tile exclusive prefix
-    uint32_t wtot_f[NWARPS];
-    uint32_t tex_f;
-    uint32_t epoch;
-    uint32_t pad;
-    uint32_t bitmap[TILE / 32 + 2];
+// Launch-wide knobs read from the workspace header.
+struct LookbackCfg {
+    uint64_t spin_limit_ns;
+    uint32_t delay_max;
+    int64_t drop_tile;
 };
 
-template <class Op, int THREADS, int ITEMS, int STAGES, int HEADS>
-constexpr int tile_smem_bytes() {
-    return STAGES * THREADS * ITEMS * static_cast<int>(sizeof(typename Op::T)) +
-           static_cast<int>(sizeof(Ctrl<Op, STAGES, THREADS / 32, THREADS * ITEMS>));
+__device__ __forceinline__ LookbackCfg read_lookback_cfg(const Header* hdr) {
+    LookbackCfg c;
+    const uint32_t lim = hdr->spin_limit_us;
+    c.spin_limit_ns = lim ? static_cast<uint64_t>(lim) * 1000ull : kDefaultSpinLimitNs;
+    c.delay_max = hdr->delay_ns_max;
+    c.drop_tile = hdr->drop_tile_plus1 - 1;
+    return c;
 }
 
-// ---------------------------------------------------------------------------
-// The tile kernel
-// ---------------------------------------------------------------------------
+// Publishes a tile's aggregate (agg_f, agg_v): state A, or for tile 0, whose
+// inclusive prefix is its aggregate, state P.  Lane 0 only.
+template <class Op>
+__device__ __forceinline__ void publish_aggregate(unsigned long long* rec, int64_t tile,
+                                                  uint32_t epoch, const LookbackCfg& cfg,
+                                                  bool agg_f, typename Op::Acc agg_v) {
+    if (tile == cfg.drop_tile) return;
+    if (cfg.delay_max) {
+        const uint32_t dly =
+            mix32(static_cast<uint64_t>(tile) * 0x9e3779b97f4a7c15ull) % (cfg.delay_max + 1);
+        if (dly) __nanosleep(dly);
+    }
+    publish<Op>(rec, tile, epoch, tile == 0 ? kStateP : kStateA, agg_f, agg_v);
+}
 
-template <class Op, int THREADS, int ITEMS, int STAGES, int MODE, int HEADS, bool REVERSE>
-__global__ void __launch_bounds__(THREADS) tile_scan_kernel(const Params p) {
-    using T = typename Op::T;
+// One backward walk of the decoupled look-back over status entries
+// base, base-1, ... (tiles or groups; `group` selects which words are read).
+// Each round, lane l reads the LB consecutive entries at distances
+// l*LB .. l*LB+LB-1 back from the round's start; the walk stops at the nearest
+// entry that ends it: an inclusive prefix, or an aggregate that contains a
+// segment head.  Entries below `floor` end the walk as the identity.  All
+// entries from the start down to the stop must be ready (at least an
+// aggregate); a round whose needed entries are not all ready is polled again,
+// re-reading only the lanes that were incomplete.  The fold of the walked
+// entries (earlier entries combined first) is returned in every lane, with
+// `real_stop` telling whether the walk ended at a status entry (true) or at
+// `floor` (false).  A wait that runs out, or a launch already aborted by
+// another wait, ends the walk early (returns false).
+template <class Op, int HEADS, int LB>
+__device__ __forceinline__ bool walk_back(unsigned long long* rec, bool group, int64_t base,
+                                          int64_t floor, uint32_t epoch, const LookbackCfg& cfg,
+                                          Header* hdr, int64_t tile, int lane, uint64_t& t0,
+                                          bool& out_f, typename Op::Acc& out_v, bool& real_stop) {
     using Acc = typename Op::Acc;
-    constexpr int TILE = THREADS * ITEMS;
-    constexpr int TILE_BYTES = TILE * static_cast<int>(sizeof(T));
-    constexpr int VEC = 16 / static_cast<int>(sizeof(T));
-    constexpr int NVEC = ITEMS / VEC;
-    constexpr int NWARPS = THREADS / 32;
-    constexpr bool DYNAMIC = (MODE == kSinglePass);
-    static_assert(ITEMS % VEC == 0, "items per thread must fill 16-byte vectors");
-    static_assert(ITEMS <= 32, "head flags are kept in one 32-bit mask");
-    static_assert(NWARPS <= 32, "warp totals are scanned by one warp");
-    static_assert(TILE_BYTES % 16 == 0, "tiles must be 16-byte multiples");
-    static_assert(!(REVERSE && HEADS == kOffsetHeads), "offset segments run forward");
-    using CtrlT = Ctrl<Op, STAGES, NWARPS, TILE>;
-
-    extern __shared__ __align__(128) unsigned char smem[];
-    CtrlT& c = *reinterpret_cast<CtrlT*>(smem + STAGES * TILE_BYTES);
-
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
-    const T* __restrict__ in = static_cast<const T*>(p.in);
-    T* out = static_cast<T*>(p.out);
-    Header* hdr = p.hdr;
-    const int64_t num_tiles = p.num_tiles;
-
-    uint64_t spin_limit_ns = kDefaultSpinLimitNs;
-    uint32_t delay_max = 0;
-    int64_t drop_tile = -1;
-    if constexpr (MODE == kSinglePass) {
-        const uint32_t lim = hdr->spin_limit_us;
-        if (lim) spin_limit_ns = static_cast<uint64_t>(lim) * 1000ull;
-        delay_max = hdr->delay_ns_max;
-        drop_tile = hdr->drop_tile_plus1 - 1;
-    }
-
-    auto claim = [&](uint32_t k) -> int64_t {
-        if constexpr (DYNAMIC)
-            return static_cast<int64_t>(atomicAdd(&hdr->tile_counter, 1u));
-        else
-            return static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(k) * gridDim.x;
-    };
-    auto phys_of = [&](int64_t tile) -> int64_t { return REVERSE ? num_tiles - 1 - tile : tile; };
-    auto count_of = [&](int64_t phys) -> int {
-        const int64_t rem = p.n - phys * TILE;
-        return rem < TILE ? static_cast<int>(rem) : TILE;
-    };
-    // Thread 0: record the k-th tile of this block in stage s and start its load.
-    auto issue = [&](int s, uint32_t k) {
-        const int64_t tile = claim(k);
-        c.tile_id[s] = tile;
-        if (tile < num_tiles) {
-            const int64_t ph = phys_of(tile);
-            if (p.fast && count_of(ph) == TILE) {
-                T* buf = reinterpret_cast<T*>(smem + s * TILE_BYTES);
-                mbar_arrive_expect_tx(&c.mbar[s], TILE_BYTES);
-                bulk_load(buf, in + ph * TILE, TILE_BYTES, &c.mbar[s]);
-            }
-        }
-    };
-
-    if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&c.mbar[s], 1);
-        fence_mbar_init();
-        c.epoch = hdr->epoch;
-    }
-    __syncthreads();
-    uint32_t epoch = (c.epoch + 1) & kEpochMask;
-    if (epoch == 0) epoch = 1;
-    if (tid == 0)
-        for (int s = 0; s < STAGES; ++s) issue(s, static_cast<uint32_t>(s));
-    __syncthreads();
-
-    uint32_t phase = 0;      // parity of each stage's mbarrier
-    int pending_refill = -1; // stage whose refill is deferred to the next iteration
-
-    for (uint32_t k = 0;; ++k) {
-        const int s = static_cast<int>(k % STAGES);
-        const int64_t tile = c.tile_id[s];
-        if (tile >= num_tiles) break;
-        const int64_t ph = phys_of(tile);
-        const int64_t tb = ph * TILE;
-        const int cnt = count_of(ph);
-        const bool tile_fast = p.fast && cnt == TILE;
-        T* buf = reinterpret_cast<T*>(smem + s * TILE_BYTES);
-
-        // ---- a1: tile load ------------------------------------------------
-        if (tile_fast) {
-            const uint32_t par = (phase >> s) & 1u;
-            phase ^= 1u << s;
-            if (!mbar_try_wait(&c.mbar[s], par)) {
-                const uint64_t t0 = global_timer_ns();
-                while (!mbar_try_wait(&c.mbar[s], par)) {
-                    if (global_timer_ns() - t0 > spin_limit_ns) {
-                        if (tid == 0) record_error(hdr, GBSCAN_ERR_TIMEOUT, tile);
-                        break;
-                    }
-                }
-            }
-        } else {
-            const int off = REVERSE ? TILE - cnt : 0;
-            for (int i = tid; i < cnt; i += THREADS) buf[off + i] = in[tb + i];
-            __syncthreads();
-        }
-
-        // Thread t owns logical items [t*ITEMS, (t+1)*ITEMS).  Forward they sit at
-        // buf[t*ITEMS + j]; reverse, logical item L sits at buf[TILE-1-L].
-        T x[ITEMS];
-        {
-            const int base = REVERSE ? TILE - (tid + 1) * ITEMS : tid * ITEMS;
-            const uint4* v4 = reinterpret_cast<const uint4*>(buf + base);
+    bool pf = false;
+    Acc pv = Op::identity();
+    real_stop = false;
+    while (true) {
+        uint32_t st[LB];
+        bool hf[LB];
+        Acc hv[LB];
+        int jstop = LB;  // this lane's first stopping entry (LB: none)
+        bool complete = false;
+        uint32_t need = 0, stop_lanes = 0;
+        uint32_t ns = 20;
+        while (true) {
+            if (!complete) {
 #pragma unroll
-            for (int v = 0; v < NVEC; ++v) {
-                const uint4 q = v4[v];
-                const T* e = reinterpret_cast<const T*>(&q);
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    if (REVERSE)
-                        x[ITEMS - 1 - (v * VEC + j)] = e[j];
-                    else
-                        x[v * VEC + j] = e[j];
-                }
-            }
-        }
-        uint32_t valid_mask = 0xffffffffu;
-        if (cnt < TILE) {
-            const int first = tid * ITEMS;
-            const int nvalid = cnt - first;
-            valid_mask = nvalid <= 0 ? 0u : (nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u));
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (!((valid_mask >> j) & 1u)) x[j] = T(0);
-        }
-
-        // Pending TMA refill of the stage used in the previous iteration: its
-        // store has had a full iteration to read shared memory.
-        if (STAGES > 1 && tid == 0 && pending_refill >= 0) {
-            bulk_wait_read_all();
-            issue(pending_refill, k - 1 + STAGES);
-            pending_refill = -1;
-        }
-
-        // ---- segment heads ----------------------------------------------
-        uint32_t hm = 0;
-        if constexpr (HEADS == kOffsetHeads) {
-            for (int i = tid; i < TILE / 32 + 2; i += THREADS) c.bitmap[i] = 0u;
-            __syncthreads();
-            const int64_t s_lo = static_cast<int64_t>(p.rec[ph].aux);
-            const int64_t s_hi = static_cast<int64_t>(p.rec[ph + 1].aux);
-            for (int64_t sg = s_lo + tid; sg < s_hi; sg += THREADS) {
-                const int64_t pos = p.offsets[sg] - tb;
-                if (pos >= 0 && pos < cnt)
-                    atomicOr(&c.bitmap[pos >> 5], 1u << (pos & 31));
-            }
-            __syncthreads();
-            const int b = tid * ITEMS;
-            const uint32_t w0 = c.bitmap[b >> 5], w1 = c.bitmap[(b >> 5) + 1];
-            const uint32_t bits = __funnelshift_r(w0, w1, b & 31);
-            hm = (ITEMS == 32 ? bits : (bits & ((1u << ITEMS) - 1u))) & valid_mask;
-        } else if constexpr (HEADS == kRowHeads) {
-            const int64_t cols = p.cols;
-            if constexpr (!REVERSE) {
-                int64_t r = (tb + static_cast<int64_t>(tid) * ITEMS) % cols;
-#pragma unroll
-                for (int j = 0; j < ITEMS; ++j) {
-                    if (r == 0) hm |= 1u << j;
-                    r = (r + 1 == cols) ? 0 : r + 1;
-                }
-            } else {
-                // logical L is physical tb + cnt - 1 - L; a head is a row's last element
-                int64_t q = (tb + cnt - static_cast<int64_t>(tid) * ITEMS) % cols;
-                if (q < 0) q += cols;
-#pragma unroll
-                for (int j = 0; j < ITEMS; ++j) {
-                    if (q == 0) hm |= 1u << j;
-                    q = (q == 0) ? cols - 1 : q - 1;
-                }
-            }
-            hm &= valid_mask;
-        }
-
-        // ---- a2: thread reduction -----------------------------------------
-        bool tf = false;
-        Acc tv = Op::identity();
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (HEADS != kNoHeads && ((hm >> j) & 1u)) {
-                tv = Op::lift(x[j]);
-                tf = true;
-            } else {
-                Op::accumulate(tv, x[j]);
-            }
-        }
-
-        // ---- a3: warp scan (inclusive, Hillis-Steele) ---------------------
-        bool wf = tf;
-        Acc wv = tv;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const bool fo = __shfl_up_sync(0xffffffffu, wf ? 1 : 0, d) != 0;
-            const Acc vo = shfl_up_acc<Op>(wv, d);
-            if (lane >= d) {
-                if (HEADS != kNoHeads)
-                    seg_combine<Op>(fo, vo, wf, wv);
-                else
-                    wv = Op::combine(vo, wv);
-            }
-        }
-        bool ef = __shfl_up_sync(0xffffffffu, wf ? 1 : 0, 1) != 0;
-        Acc ev = shfl_up_acc<Op>(wv, 1);
-        if (lane == 0) {
-            ef = false;
-            ev = Op::identity();
-        }
-        if (lane == 31) {
-            c.wtot_v[warp] = wv;
-            c.wtot_f[warp] = wf ? 1u : 0u;
-        }
-        __syncthreads();  // sync 1: warp totals
-
-        // ---- a4/a5: block scan of warp totals, then look-back (warp 0) -----
-        if (warp == 0) {
-            bool bf = lane < NWARPS ? c.wtot_f[lane] != 0 : false;
-            Acc bv = lane < NWARPS ? c.wtot_v[lane] : Op::identity();
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const bool fo = __shfl_up_sync(0xffffffffu, bf ? 1 : 0, d) != 0;
-                const Acc vo = shfl_up_acc<Op>(bv, d);
-                if (lane >= d) {
-                    if (HEADS != kNoHeads)
-                        seg_combine<Op>(fo, vo, bf, bv);
-                    else
-                        bv = Op::combine(vo, bv);
-                }
-            }
-            // tile aggregate: inclusive value at lane NWARPS-1
-            const bool agg_f = __shfl_sync(0xffffffffu, bf ? 1 : 0, NWARPS - 1) != 0;
-            const Acc agg_v = shfl_idx_acc<Op>(bv, NWARPS - 1);
-            // exclusive prefix of each warp within the tile
-            bool xf = __shfl_up_sync(0xffffffffu, bf ? 1 : 0, 1) != 0;
-            Acc xv = shfl_up_acc<Op>(bv, 1);
-            if (lane == 0) {
-                xf = false;
-                xv = Op::identity();
-            }
-            if (lane < NWARPS) {
-                c.wtot_v[lane] = xv;
-                c.wtot_f[lane] = xf ? 1u : 0u;
-            }
-
-            bool pf = false;  // tile exclusive prefix
-            Acc pv = Op::identity();
-            if constexpr (MODE == kReduce) {
-                if (lane == 0) p.rec[tile].aux = static_cast<unsigned long long>(Op::to_bits(agg_v));
-            } else if constexpr (MODE == kScanOffset) {
-                pv = Op::from_bits(static_cast<typename Op::Bits>(p.rec[tile].aux));
-            } else {
-                const bool dropped = (tile == drop_tile);
-                const uint32_t dly = delay_max ? mix32(static_cast<uint64_t>(tile) * 0x9e3779b97f4a7c15ull) % (delay_max + 1) : 0u;
-                if (tile == 0) {
-                    if (lane == 0 && !dropped) {
-                        if (dly) __nanosleep(dly);
-                        publish<Op>(p.rec, tile, epoch, kStateP, agg_f, agg_v);
-                    }
-                } else {
-                    if (lane == 0 && !dropped) {
-                        if (dly) __nanosleep(dly);
-                        publish<Op>(p.rec, tile, epoch, kStateA, agg_f, agg_v);
-                    }
-                    int64_t base = tile - 1;
-                    uint64_t t0 = 0;
-                    bool gave_up = false;
-                    while (true) {
-                        const int64_t idx = base - lane;
-                        uint32_t st;
-                        bool hf;
-                        Acc hv;
-                        uint32_t need, stop;
-                        uint32_t ns = 32;
-                        while (true) {
-                            if (idx >= 0) {
-                                read_status<Op>(p.rec, idx, epoch, st, hf, hv);
-                            } else {
-                                st = kStateP;  // before the first tile: the identity
-                                hf = false;
-                                hv = Op::identity();
-                            }
-                            const uint32_t valid = __ballot_sync(0xffffffffu, st != kStateX);
-                            stop = __ballot_sync(0xffffffffu,
-                                                 st == kStateP || (st == kStateA && hf));
-                            need = stop ? (((stop & (0u - stop)) << 1) - 1u) : 0xffffffffu;
-                            if ((valid & need) == need) break;
-                            // bounded wait: give up after the spin limit or once
-                            // another tile has recorded an error
-                            int quit = 0;
-                            if (lane == 0) {
-                                const uint64_t now = global_timer_ns();
-                                if (t0 == 0) t0 = now;
-                                if (now - t0 > spin_limit_ns) {
-                                    record_error(hdr, GBSCAN_ERR_TIMEOUT, tile);
-                                    quit = 1;
-                                } else if (ld_relaxed_s32(&hdr->error) != 0) {
-                                    quit = 1;
-                                }
-                            }
-                            if (__shfl_sync(0xffffffffu, quit, 0)) {
-                                gave_up = true;
-                                break;
-                            }
-                            __nanosleep(ns);
-                            ns = ns < 512 ? ns * 2 : 512;
-                        }
-                        if (gave_up) break;
-                        // fold lanes need..0 in tile order (higher lane = earlier tile)
-                        bool rf = ((need >> lane) & 1u) ? hf : false;
-                        Acc rv = ((need >> lane) & 1u) ? hv : Op::identity();
-#pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const bool fo = __shfl_down_sync(0xffffffffu, rf ? 1 : 0, d) != 0;
-                            const Acc vo = shfl_down_acc<Op>(rv, d);
-                            if (lane + d < 32) {
-                                if (HEADS != kNoHeads)
-                                    seg_combine<Op>(fo, vo, rf, rv);
-                                else
-                                    rv = Op::combine(vo, rv);
-                            }
-                        }
-                        const bool wf0 = __shfl_sync(0xffffffffu, rf ? 1 : 0, 0) != 0;
-                        const Acc wv0 = shfl_idx_acc<Op>(rv, 0);
-                        if (HEADS != kNoHeads)
-                            seg_combine<Op>(wf0, wv0, pf, pv);
+                for (int j = 0; j < LB; ++j) {
+                    const int64_t idx = base - static_cast<int64_t>(lane) * LB - j;
+                    if (idx >= floor) {
+                        if (group)
+                            read_words<Op>(rec_glo(rec, idx), rec_ghi(rec, idx), epoch, st[j], hf[j], hv[j]);
                         else
-                            pv = Op::combine(wv0, pv);
-                        if (stop) break;
-                        base -= 32;
-                    }
-                    bool incf = agg_f;
-                    Acc incv = agg_v;
-                    if (HEADS != kNoHeads)
-                        seg_combine<Op>(pf, pv, incf, incv);
-                    else
-                        incv = Op::combine(pv, incv);
-                    if (lane == 0 && !dropped) {
-                        if (dly) __nanosleep(dly);
-                        publish<Op>(p.rec, tile, epoch, kStateP, incf, incv);
+                            read_words<Op>(rec_lo(rec, idx), rec_hi(rec, idx), epoch, st[j], hf[j], hv[j]);
+                    } else {
+                        st[j] = kStateP;  // below the floor: the identity
+                        hf[j] = false;
+                        hv[j] = Op::identity();
                     }
                 }
+                jstop = LB;
+#pragma unroll
+                for (int j = LB - 1; j >= 0; --j)
+                    if (st[j] == kStateP || (st[j] == kStateA && hf[j])) jstop = j;
+                complete = true;
+#pragma unroll
+                for (int j = 0; j < LB; ++j)
+                    if (j <= jstop && st[j] == kStateX) complete = false;
             }
+            stop_lanes = __ballot_sync(0xffffffffu, jstop < LB);
+            need = stop_lanes ? (((stop_lanes & (0u - stop_lanes)) << 1) - 1u) : 0xffffffffu;
+            const uint32_t incomplete = __ballot_sync(0xffffffffu, !complete);
+            if ((incomplete & need) == 0) break;
+            // bounded wait: give up after the spin limit or once another wait
+            // has aborted the launch
+            int quit = 0;
             if (lane == 0) {
-                c.tex_v = pv;
-                c.tex_f = pf ? 1u : 0u;
-            }
-        }
-        __syncthreads();  // sync 2: tile prefix and warp prefixes ready
-
-        if constexpr (MODE == kReduce) {
-            // every thread read its items before sync 1: the stage is free
-            if (tid == 0) issue(s, k + STAGES);
-            if (STAGES == 1) __syncthreads();
-            continue;
-        }
-
-        // ---- a6: carry add, outputs into shared memory -----------------------
-        bool cf = c.wtot_f[warp] != 0;  // warp's prefix within the tile
-        Acc cv = c.wtot_v[warp];
-        {
-            if (HEADS != kNoHeads)
-                seg_combine<Op>(cf, cv, ef, ev);
-            else
-                ev = Op::combine(cv, ev);
-            // ev/ef: thread exclusive prefix within the tile
-            bool gf = ef;
-            Acc gv = ev;
-            const bool tf2 = c.tex_f != 0;
-            const Acc tv2 = c.tex_v;
-            if (HEADS != kNoHeads)
-                seg_combine<Op>(tf2, tv2, gf, gv);
-            else
-                gv = Op::combine(tv2, gv);
-            // (gf, gv): everything before this thread's first item.  A local
-            // head (rf) makes later items independent of it.
-            bool rf = false;
-            Acc rv = Op::identity();
-            const bool excl = p.exclusive != 0;
-            T y[ITEMS];
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const bool h = HEADS != kNoHeads && ((hm >> j) & 1u);
-                if (excl) {
-                    if (h)
-                        y[j] = T(0);
-                    else if (rf)
-                        y[j] = Op::output1(rv);
-                    else
-                        y[j] = Op::output(gv, rv);
+                const uint64_t now = global_timer_ns();
+                if (t0 == 0) t0 = now;
+                if (now - t0 > cfg.spin_limit_ns) {
+                    record_timeout(hdr, epoch, tile);
+                    quit = 1;
+                } else if (launch_aborted(hdr, epoch)) {
+                    quit = 1;
                 }
-                if (h) {
-                    rv = Op::lift(x[j]);
-                    rf = true;
-                } else {
-                    Op::accumulate(rv, x[j]);
+            }
+            if (__shfl_sync(0xffffffffu, quit, 0)) {
+                out_f = pf;
+                out_v = pv;
+                return false;
+            }
+            __nanosleep(ns);
+            ns = ns < 160 ? ns * 2 : 160;
+            poll_round_fence();
+        }
+        // this lane's share, earliest entry first (higher j = earlier)
+        bool rf = false;
+        Acc rv = Op::identity();
+        if ((need >> lane) & 1u) {
+#pragma unroll
+            for (int j = LB - 1; j >= 0; --j) {
+                if (j <= jstop) {
+                    if (HEADS != kNoHeads) {
+                        bool f2 = hf[j];
+                        Acc v2 = hv[j];
+                        seg_combine<Op>(rf, rv, f2, v2);
+                        rf = f2;
+                        rv = v2;
+                    } else {
+                        rv = Op::combine(rv, hv[j]);
+                    }
                 }
-                if (!excl) y[j] = rf ? Op::output1(rv) : Op::output(gv, rv);
-            }
-            const int base = REVERSE ? TILE - (tid + 1) * ITEMS : tid * ITEMS;
-            uint4* v4 = reinterpret_cast<uint4*>(buf + base);
-#pragma unroll
-            for (int v = 0; v < NVEC; ++v) {
-                uint4 q;
-                T* e = reinterpret_cast<T*>(&q);
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) e[j] = REVERSE ? y[ITEMS - 1 - (v * VEC + j)] : y[v * VEC + j];
-                v4[v] = q;
             }
         }
-        if (tile_fast) fence_proxy_async_smem();
-        __syncthreads();  // sync 3: outputs in shared memory
-
-        if (tile_fast) {
-            if (tid == 0) {
-                bulk_store(out + tb, buf, TILE_BYTES);
-                bulk_commit();
-            }
-        } else {
-            const int off = REVERSE ? TILE - cnt : 0;
-            for (int i = tid; i < cnt; i += THREADS) out[tb + i] = buf[off + i];
-            __syncthreads();
-        }
-        if (STAGES == 1) {
-            if (tid == 0) {
-                if (tile_fast) bulk_wait_read_all();
-                issue(s, k + 1);
-            }
-            __syncthreads();
-        } else {
-            pending_refill = s;  // thread 0 refills it next iteration
-        }
-    }
-
-    // ---- block exit: the last block to finish resets the launch state -----
-    if (tid == 0) {
-        bulk_wait_all();
-        c.pad = 0u;
-        if constexpr (MODE == kSinglePass) {
-            __threadfence();
-            const uint32_t prev = atomicAdd(&hdr->done_counter, 1u);
-            if (prev == gridDim.x - 1) {
-                __threadfence();
-                hdr->tile_counter = 0;
-                hdr->done_counter = 0;
-                // The next launch tags its words with epoch + 1.  Before the tag
-                // wraps, clear every status word so that no word written 2^29
-                // launches ago can pass for a current one.
-                const bool wrap = (epoch == kEpochMask);
-                hdr->epoch = wrap ? 0u : epoch;
-                c.pad = wrap ? 1u : 0u;
-            }
-        }
-    }
-    if constexpr (MODE == kSinglePass) {
-        __syncthreads();
-        if (c.pad) {
-            for (int64_t i = tid; i < p.rec_capacity; i += THREADS) p.rec[i].word = 0ull;
-            __threadfence();
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Two-pass helper: exclusive scan of the tile sums (record aux fields), one block.
-// ---------------------------------------------------------------------------
-
-template <class Op, int THREADS>
-__global__ void __launch_bounds__(THREADS) scan_tile_sums_kernel(TileRecord* rec, int64_t num_tiles) {
-    using Acc = typename Op::Acc;
-    constexpr int NWARPS = THREADS / 32;
-    __shared__ Acc wsum[NWARPS];
-    __shared__ Acc carry_s;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    Acc carry = Op::identity();
-    for (int64_t base = 0; base < num_tiles; base += THREADS) {
-        const int64_t i = base + tid;
-        Acc v = i < num_tiles ? Op::from_bits(static_cast<typename Op::Bits>(rec[i].aux))
-                              : Op::identity();
-        Acc inc = v;
+        // fold the lanes in order (higher lane = earlier entries)
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const Acc o = shfl_up_acc<Op>(inc, d);
-            if (lane >= d) inc = Op::combine(o, inc);
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            Acc w = lane < NWARPS ? wsum[lane] : Op::identity();
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const Acc o = shfl_up_acc<Op>(w, d);
-                if (lane >= d) w = Op::combine(o, w);
+            const bool fo = __shfl_down_sync(0xffffffffu, rf ? 1 : 0, d) != 0;
+            const Acc vo = shfl_down_acc<Op>(rv, d);
+            if (lane + d < 32) {
+                if (HEADS != kNoHeads)
+                    seg_combine<Op>(fo, vo, rf, rv);
+                else
+                    rv = Op::combine(vo, rv);
             }
-            Acc wx = shfl_up_acc<Op>(w, 1);
-            if (lane == 0) wx = Op::identity();
-            if (lane < NWARPS) wsum[lane] = wx;
-            const Acc total = shfl_idx_acc<Op>(w, NWARPS - 1);
-            if (lane == 0) carry_s = Op::combine(carry, total);
         }
-        __syncthreads();
-        Acc ex = shfl_up_acc<Op>(inc, 1);
-        if (lane == 0) ex = Op::identity();
-        ex = Op::combine(wsum[warp], ex);
-        ex = Op::combine(carry, ex);
-        if (i < num_tiles) rec[i].aux = static_cast<unsigned long long>(Op::to_bits(ex));
-        carry = carry_s;
-        __syncthreads();
+        const bool wf0 = __shfl_sync(0xffffffffu, rf ? 1 : 0, 0) != 0;
+        const Acc wv0 = shfl_idx_acc<Op>(rv, 0);
+        if (HEADS != kNoHeads)
+            seg_combine<Op>(wf0, wv0, pf, pv);
+        else
+            pv = Op::combine(wv0, pv);
+        if (stop_lanes) {
+            // the stop is real unless it is the first entry below the floor
+            const int sl = __ffs(stop_lanes) - 1;
+            const int js = __shfl_sync(0xffffffffu, jstop, sl);
+            real_stop = (base - static_cast<int64_t>(sl) * LB - js) >= floor;
+            break;
+        }
+        base -= 32 * LB;
     }
+    out_f = pf;
+    out_v = pv;
+    return true;
+}
+
+// Finds the exclusive prefix of `tile` and publishes the tile's inclusive
+// prefix (its aggregate must already be published), in two levels:
+//   1. the tile's own group (16 tiles): walk back over the tiles of the group
+//      before this one; a stop there settles the prefix.  If the walk reaches
+//      the group start and this is the group's last tile, the fold plus the
+//      tile's own aggregate is the group aggregate: publish it.
+//   2. earlier groups: walk back over group status words (32 * LBG groups per
+//      round) to the nearest group inclusive prefix.
+// The group's last tile also publishes its inclusive prefix as the group's.
+// So a look-back costs about two round trips however many tiles are in
+// flight.  A wait that runs out (or a launch already aborted by another wait)
+// ends the look-back with the prefix found so far, which is then wrong, but
+// successors are released and the launch finishes; the host learns of it from
+// the workspace.  Returns the exclusive prefix in every lane.
+template <class Op, int HEADS, int LB>
+__device__ __forceinline__ void lookback(unsigned long long* rec, Header* hdr, int64_t tile,
+                                         uint32_t epoch, const LookbackCfg& cfg, bool agg_f,
+                                         typename Op::Acc agg_v, int lane, bool& out_f,
+                                         typename Op::Acc& out_v) {
+    using Acc = typename Op::Acc;
+    const bool dropped = (tile == cfg.drop_tile);
+    const int64_t g = tile / kGroup;
+    const bool last_in_group = (tile % kGroup) == kGroup - 1;
+    bool pf = false;
+    Acc pv = Op::identity();
+    uint64_t t0 = 0;
+    bool real = false;
+    bool ok = true;
+    if (tile % kGroup != 0) {
+        ok = walk_back<Op, HEADS, 1>(rec, false, tile - 1, g * kGroup, epoch, cfg, hdr, tile, lane,
+                                     t0, pf, pv, real);
+        if (ok && !real && last_in_group && lane == 0 && !dropped) {
+            bool gf = agg_f;
+            Acc gv = agg_v;
+            if (HEADS != kNoHeads)
+                seg_combine<Op>(pf, pv, gf, gv);
+            else
+                gv = Op::combine(pv, gv);
+            publish_group<Op>(rec, g, epoch, kStateA, gf, gv);
+        }
+    } else if (last_in_group && lane == 0 && !dropped) {
+        publish_group<Op>(rec, g, epoch, kStateA, agg_f, agg_v);  // one-tile groups
+    }
+    if (ok && !real && g > 0) {
+        bool qf;
+        Acc qv;
+        ok = walk_back<Op, HEADS, LB>(rec, true, g - 1, 0, epoch, cfg, hdr, tile, lane, t0, qf, qv,
+                                      real);
+        if (HEADS != kNoHeads)
+            seg_combine<Op>(qf, qv, pf, pv);
+        else
+            pv = Op::combine(qv, pv);
+    }
+    bool incf = agg_f;
+    Acc incv = agg_v;
+    if (HEADS != kNoHeads)
+        seg_combine<Op>(pf, pv, incf, incv);
+    else
+        incv = Op::combine(pv, incv);
+    if (lane == 0 && !dropped && tile != 0) {
+        if (cfg.delay_max) {
+            const uint32_t dly =
+                mix32(static_cast<uint64_t>(tile) * 0xc2b2ae3d27d4eb4full) % (cfg.delay_max + 1);
+            if (dly) __nanosleep(dly);
+        }
+        publish<Op>(rec, tile, epoch, kStateP, incf, incv);
+    }
+    if (last_in_group && lane == 0 && !dropped) publish_group<Op>(rec, g, epoch, kStateP, incf, incv);
+    out_f = pf;
+    out_v = pv;
+}
+
+// Epoch bookkeeping at the end of a single-pass launch: the last block to
+// finish resets the tile counter and records the epoch; before the 29-bit tag
+// wraps it clears every status word, so that no word written 2^29 launches
+// ago can pass for a current one.  Called by one thread per block; returns
+// true in the block that must clear.
+__device__ __forceinline__ bool finish_launch(Header* hdr, uint32_t epoch) {
+    __threadfence();
+    const uint32_t prev = atomicAdd(&hdr->done_counter, 1u);
+    if (prev != gridDim.x - 1) return false;
+    __threadfence();
+    hdr->tile_counter = 0;
+    hdr->done_counter = 0;
+    const bool wrap = (epoch == kEpochMask);
+    hdr->epoch = wrap ? 0u : epoch;
+    if (wrap) hdr->abort_epoch = 0u;
+    return wrap;
+}
+
+__device__ __forceinline__ uint32_t launch_epoch(uint32_t completed) {
+    const uint32_t e = (completed + 1) & kEpochMask;
+    return e == 0 ? 1u : e;
 }
 
 }  // namespace gbscan

@@ -4,16 +4,17 @@
 #include <atomic>
 #include <cstdint>
 
-#include "gbscan_device.cuh"
+#include "kernels.cuh"
 
 namespace gbscan {
 
 using LaunchFn = cudaError_t (*)(const Params&, cudaStream_t);
-using SumsFn = cudaError_t (*)(TileRecord*, int64_t, cudaStream_t);
+using SumsFn = cudaError_t (*)(unsigned long long*, int64_t, cudaStream_t);
 
 // One launch shape of a kernel family.
 struct Variant {
-    int threads, items, stages, tile;
+    int threads, items, stages, tile;  // single-pass kernel: block threads (with the
+                                       // loader warp and one agent warp per stage)
     LaunchFn single_pass;  // chained scan with decoupled look-back
     LaunchFn reduce;       // two-pass: tile sums (null where not built)
     LaunchFn scan_offset;  // two-pass: scan with the scanned tile sums
@@ -27,14 +28,12 @@ struct Family {
 
 int device_sm_count(int device);
 
-// Launch a tile kernel as a persistent grid: one block per resident slot,
-// never more blocks than tiles.  Shared-memory opt-in and occupancy are
-// queried once per device and kernel.
-template <class Op, int THREADS, int ITEMS, int STAGES, int MODE, int HEADS, bool REVERSE>
-cudaError_t launch_tile(const Params& p, cudaStream_t stream) {
-    auto kern = tile_scan_kernel<Op, THREADS, ITEMS, STAGES, MODE, HEADS, REVERSE>;
-    constexpr int smem = tile_smem_bytes<Op, THREADS, ITEMS, STAGES, HEADS>();
-    static std::atomic<int> occ_cache[64];
+// Launch a kernel as a persistent grid: one block per resident slot, never
+// more blocks than tiles.  Shared-memory opt-in and occupancy are queried once
+// per device and kernel.
+template <class Kernel>
+cudaError_t launch_persistent(Kernel kern, int threads, int smem, std::atomic<int>* occ_cache,
+                              const Params& p, cudaStream_t stream) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -42,7 +41,7 @@ cudaError_t launch_tile(const Params& p, cudaStream_t stream) {
     if (occ <= 0) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
         if (e != cudaSuccess) return e;
         if (occ <= 0) return cudaErrorInvalidConfiguration;
         if (dev >= 0 && dev < 64) occ_cache[dev].store(occ, std::memory_order_relaxed);
@@ -52,29 +51,46 @@ cudaError_t launch_tile(const Params& p, cudaStream_t stream) {
     int64_t grid = static_cast<int64_t>(sms) * occ;
     if (grid > p.num_tiles) grid = p.num_tiles;
     if (grid < 1) grid = 1;
-    kern<<<static_cast<unsigned>(grid), THREADS, smem, stream>>>(p);
+    kern<<<static_cast<unsigned>(grid), threads, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
+template <class Op, int CWARPS, int ITEMS, int STAGES, int HEADS, bool REVERSE, int LB, int MINB>
+cudaError_t launch_ws(const Params& p, cudaStream_t stream) {
+    static std::atomic<int> occ_cache[64];
+    return launch_persistent(ws_scan_kernel<Op, CWARPS, ITEMS, STAGES, HEADS, REVERSE, LB, MINB>,
+                             ws_threads<CWARPS, STAGES>(), ws_smem_bytes<Op, CWARPS, ITEMS, STAGES>(),
+                             occ_cache, p, stream);
+}
+
+template <class Op, int THREADS, int ITEMS, int STAGES, int MODE>
+cudaError_t launch_tp(const Params& p, cudaStream_t stream) {
+    static std::atomic<int> occ_cache[64];
+    return launch_persistent(two_pass_kernel<Op, THREADS, ITEMS, STAGES, MODE>, THREADS,
+                             tp_smem_bytes<Op, THREADS, ITEMS, STAGES>(), occ_cache, p, stream);
+}
+
 template <class Op>
-cudaError_t launch_scan_sums(TileRecord* rec, int64_t num_tiles, cudaStream_t stream) {
+cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStream_t stream) {
     scan_tile_sums_kernel<Op, 1024><<<1, 1024, 0, stream>>>(rec, num_tiles);
     return cudaGetLastError();
 }
 
-// Variant descriptors.  VEC-filling item counts: 4-byte elements take multiples
-// of 4 items, 8-byte elements multiples of 2; an odd number of 16-byte vectors
-// per thread keeps the 128-bit shared-memory reads bank-conflict free.
-#define GBSCAN_VARIANT_SP(OP, T_, I_, S_, HEADS_, REV_)                                     \
-    Variant {                                                                              \
-        T_, I_, S_, T_ * I_, &launch_tile<OP, T_, I_, S_, kSinglePass, HEADS_, REV_>, nullptr, \
-            nullptr                                                                        \
+// Variant descriptors.  A variant names the single-pass kernel's shape
+// (consumer warps CW, items per thread I, pipeline stages S, look-back tiles per
+// lane LB, minimum resident blocks MB) and, for plain scans, the two-pass
+// kernels of the same tile (CW * 32 threads, I items, TS stages).  Item counts
+// fill whole 16-byte vectors, an odd number of them per thread so that the
+// 128-bit shared-memory reads are bank-conflict free.
+#define GBSCAN_VARIANT_SP(OP, CW, I, S, LB, MB, HEADS_, REV_)                                   \
+    Variant {                                                                                  \
+        (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, HEADS_, REV_, LB, MB>, nullptr, \
+            nullptr                                                                            \
     }
-#define GBSCAN_VARIANT_ALL(OP, T_, I_, S_)                                          \
-    Variant {                                                                      \
-        T_, I_, S_, T_ * I_, &launch_tile<OP, T_, I_, S_, kSinglePass, kNoHeads, false>, \
-            &launch_tile<OP, T_, I_, S_, kReduce, kNoHeads, false>,                \
-            &launch_tile<OP, T_, I_, S_, kScanOffset, kNoHeads, false>             \
+#define GBSCAN_VARIANT_ALL(OP, CW, I, S, LB, MB, TS)                                          \
+    Variant {                                                                                 \
+        (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, kNoHeads, false, LB, MB>, \
+            &launch_tp<OP, CW * 32, I, TS, kReduce>, &launch_tp<OP, CW * 32, I, TS, kScanOffset> \
     }
 
 // Families, one per translation unit group.
@@ -92,7 +108,7 @@ const Family& family_rows_rev_f64();
 
 // Smallest tile (in elements) of any variant for an element size: sizes the
 // workspace so that every variant fits.
-constexpr int kMinTile4 = 256 * 12;
+constexpr int kMinTile4 = 256 * 12;  // 8 consumer warps x 12 items
 constexpr int kMinTile8 = 256 * 6;
 
 }  // namespace gbscan

@@ -5,20 +5,24 @@
 namespace gbscan {
 
 static const Variant kScanF32[] = {
-    GBSCAN_VARIANT_ALL(OpF32, 256, 20, 2),
-    GBSCAN_VARIANT_ALL(OpF32, 256, 12, 3),
-    GBSCAN_VARIANT_ALL(OpF32, 512, 20, 1),
+    GBSCAN_VARIANT_ALL(OpF32, 8, 20, 3, 8, 3, 2),
+    GBSCAN_VARIANT_ALL(OpF32, 8, 20, 4, 8, 2, 2),
+    GBSCAN_VARIANT_ALL(OpF32, 8, 12, 4, 8, 3, 3),
+    GBSCAN_VARIANT_ALL(OpF32, 16, 20, 2, 8, 2, 1),
+    GBSCAN_VARIANT_ALL(OpF32, 4, 28, 4, 16, 4, 3),
 };
+
 const Family& family_scan_f32() {
-    static const Family f{3, kScanF32, &launch_scan_sums<OpF32>};
+    static const Family f{5, kScanF32, &launch_scan_sums<OpF32>};
     return f;
 }
 
 static const Variant kSegF32[] = {
-    GBSCAN_VARIANT_SP(OpF32, 256, 20, 2, kOffsetHeads, false),
-    GBSCAN_VARIANT_SP(OpF32, 256, 12, 3, kOffsetHeads, false),
-    GBSCAN_VARIANT_SP(OpF32, 512, 20, 1, kOffsetHeads, false),
+    GBSCAN_VARIANT_SP(OpF32, 8, 20, 3, 8, 3, kOffsetHeads, false),
+    GBSCAN_VARIANT_SP(OpF32, 8, 20, 4, 8, 2, kOffsetHeads, false),
+    GBSCAN_VARIANT_SP(OpF32, 16, 20, 2, 8, 2, kOffsetHeads, false),
 };
+
 const Family& family_seg_f32() {
     static const Family f{3, kSegF32, nullptr};
     return f;

@@ -4,12 +4,15 @@
 namespace gbscan {
 
 static const Variant kScanF64[] = {
-    GBSCAN_VARIANT_ALL(OpF64, 256, 10, 2),
-    GBSCAN_VARIANT_ALL(OpF64, 256, 6, 3),
-    GBSCAN_VARIANT_ALL(OpF64, 512, 10, 1),
+    GBSCAN_VARIANT_ALL(OpF64, 8, 10, 3, 8, 3, 2),
+    GBSCAN_VARIANT_ALL(OpF64, 8, 10, 4, 8, 2, 2),
+    GBSCAN_VARIANT_ALL(OpF64, 8, 6, 4, 8, 3, 3),
+    GBSCAN_VARIANT_ALL(OpF64, 16, 10, 2, 8, 2, 1),
+    GBSCAN_VARIANT_ALL(OpF64, 4, 14, 4, 16, 4, 3),
 };
+
 const Family& family_scan_f64() {
-    static const Family f{3, kScanF64, &launch_scan_sums<OpF64>};
+    static const Family f{5, kScanF64, &launch_scan_sums<OpF64>};
     return f;
 }
 

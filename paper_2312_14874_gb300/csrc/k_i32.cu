@@ -5,20 +5,24 @@
 namespace gbscan {
 
 static const Variant kScanI32[] = {
-    GBSCAN_VARIANT_ALL(OpI32, 256, 20, 2),
-    GBSCAN_VARIANT_ALL(OpI32, 256, 12, 3),
-    GBSCAN_VARIANT_ALL(OpI32, 512, 20, 1),
+    GBSCAN_VARIANT_ALL(OpI32, 8, 20, 3, 8, 3, 2),
+    GBSCAN_VARIANT_ALL(OpI32, 8, 20, 4, 8, 2, 2),
+    GBSCAN_VARIANT_ALL(OpI32, 8, 12, 4, 8, 3, 3),
+    GBSCAN_VARIANT_ALL(OpI32, 16, 20, 2, 8, 2, 1),
+    GBSCAN_VARIANT_ALL(OpI32, 4, 28, 4, 16, 4, 3),
 };
+
 const Family& family_scan_i32() {
-    static const Family f{3, kScanI32, &launch_scan_sums<OpI32>};
+    static const Family f{5, kScanI32, &launch_scan_sums<OpI32>};
     return f;
 }
 
 static const Variant kSegI32[] = {
-    GBSCAN_VARIANT_SP(OpI32, 256, 20, 2, kOffsetHeads, false),
-    GBSCAN_VARIANT_SP(OpI32, 256, 12, 3, kOffsetHeads, false),
-    GBSCAN_VARIANT_SP(OpI32, 512, 20, 1, kOffsetHeads, false),
+    GBSCAN_VARIANT_SP(OpI32, 8, 20, 3, 8, 3, kOffsetHeads, false),
+    GBSCAN_VARIANT_SP(OpI32, 8, 20, 4, 8, 2, kOffsetHeads, false),
+    GBSCAN_VARIANT_SP(OpI32, 16, 20, 2, 8, 2, kOffsetHeads, false),
 };
+
 const Family& family_seg_i32() {
     static const Family f{3, kSegI32, nullptr};
     return f;

@@ -5,38 +5,44 @@
 namespace gbscan {
 
 static const Variant kRowsF32[] = {
-    GBSCAN_VARIANT_SP(OpF32, 256, 20, 2, kRowHeads, false),
-    GBSCAN_VARIANT_SP(OpF32, 256, 12, 3, kRowHeads, false),
-    GBSCAN_VARIANT_SP(OpF32, 512, 20, 1, kRowHeads, false),
+    GBSCAN_VARIANT_SP(OpF32, 8, 20, 3, 8, 3, kRowHeads, false),
+    GBSCAN_VARIANT_SP(OpF32, 8, 20, 4, 8, 2, kRowHeads, false),
+    GBSCAN_VARIANT_SP(OpF32, 16, 20, 2, 8, 2, kRowHeads, false),
 };
+
 static const Variant kRowsRevF32[] = {
-    GBSCAN_VARIANT_SP(OpF32, 256, 20, 2, kRowHeads, true),
-    GBSCAN_VARIANT_SP(OpF32, 256, 12, 3, kRowHeads, true),
-    GBSCAN_VARIANT_SP(OpF32, 512, 20, 1, kRowHeads, true),
+    GBSCAN_VARIANT_SP(OpF32, 8, 20, 3, 8, 3, kRowHeads, true),
+    GBSCAN_VARIANT_SP(OpF32, 8, 20, 4, 8, 2, kRowHeads, true),
+    GBSCAN_VARIANT_SP(OpF32, 16, 20, 2, 8, 2, kRowHeads, true),
 };
+
 static const Variant kRowsF64[] = {
-    GBSCAN_VARIANT_SP(OpF64, 256, 10, 2, kRowHeads, false),
-    GBSCAN_VARIANT_SP(OpF64, 256, 6, 3, kRowHeads, false),
-    GBSCAN_VARIANT_SP(OpF64, 512, 10, 1, kRowHeads, false),
+    GBSCAN_VARIANT_SP(OpF64, 8, 10, 3, 8, 3, kRowHeads, false),
+    GBSCAN_VARIANT_SP(OpF64, 8, 10, 4, 8, 2, kRowHeads, false),
+    GBSCAN_VARIANT_SP(OpF64, 16, 10, 2, 8, 2, kRowHeads, false),
 };
+
 static const Variant kRowsRevF64[] = {
-    GBSCAN_VARIANT_SP(OpF64, 256, 10, 2, kRowHeads, true),
-    GBSCAN_VARIANT_SP(OpF64, 256, 6, 3, kRowHeads, true),
-    GBSCAN_VARIANT_SP(OpF64, 512, 10, 1, kRowHeads, true),
+    GBSCAN_VARIANT_SP(OpF64, 8, 10, 3, 8, 3, kRowHeads, true),
+    GBSCAN_VARIANT_SP(OpF64, 8, 10, 4, 8, 2, kRowHeads, true),
+    GBSCAN_VARIANT_SP(OpF64, 16, 10, 2, 8, 2, kRowHeads, true),
 };
 
 const Family& family_rows_f32() {
     static const Family f{3, kRowsF32, nullptr};
     return f;
 }
+
 const Family& family_rows_rev_f32() {
     static const Family f{3, kRowsRevF32, nullptr};
     return f;
 }
+
 const Family& family_rows_f64() {
     static const Family f{3, kRowsF64, nullptr};
     return f;
 }
+
 const Family& family_rows_rev_f64() {
     static const Family f{3, kRowsRevF64, nullptr};
     return f;

@@ -1,0 +1,199 @@
+// tile_common.cuh — per-thread pieces shared by the tile kernels: moving a
+// thread's items between shared memory and registers, segment heads, the
+// sequential thread scan, the warp scan, and the per-element outputs.
+#pragma once
+
+#include "gbscan_device.cuh"
+
+namespace gbscan {
+
+// Thread t owns the logical items [t*ITEMS, (t+1)*ITEMS) of a tile.  Forward,
+// logical item L sits at buf[L]; reverse, at buf[TILE-1-L] (a partial tile is
+// stored right-aligned, so the same mapping holds).  The 16-byte reads of a
+// thread are contiguous; with an odd number of vectors per thread, the eight
+// lanes of a shared-memory wavefront hit eight different 16-byte bank groups.
+template <class T, int ITEMS, int TILE, bool REVERSE>
+__device__ __forceinline__ void load_items(const T* buf, int tid, T (&x)[ITEMS]) {
+    constexpr int VEC = 16 / static_cast<int>(sizeof(T));
+    constexpr int NVEC = ITEMS / VEC;
+    const int base = REVERSE ? TILE - (tid + 1) * ITEMS : tid * ITEMS;
+    const uint4* v4 = reinterpret_cast<const uint4*>(buf + base);
+#pragma unroll
+    for (int v = 0; v < NVEC; ++v) {
+        const uint4 q = v4[v];
+        const T* e = reinterpret_cast<const T*>(&q);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            if (REVERSE)
+                x[ITEMS - 1 - (v * VEC + j)] = e[j];
+            else
+                x[v * VEC + j] = e[j];
+        }
+    }
+}
+
+template <class T, int ITEMS, int TILE, bool REVERSE>
+__device__ __forceinline__ void store_items(T* buf, int tid, const T (&y)[ITEMS]) {
+    constexpr int VEC = 16 / static_cast<int>(sizeof(T));
+    constexpr int NVEC = ITEMS / VEC;
+    const int base = REVERSE ? TILE - (tid + 1) * ITEMS : tid * ITEMS;
+    uint4* v4 = reinterpret_cast<uint4*>(buf + base);
+#pragma unroll
+    for (int v = 0; v < NVEC; ++v) {
+        uint4 q;
+        T* e = reinterpret_cast<T*>(&q);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) e[j] = REVERSE ? y[ITEMS - 1 - (v * VEC + j)] : y[v * VEC + j];
+        v4[v] = q;
+    }
+}
+
+// Bit j set: the thread's item j is inside the tile's cnt valid elements.
+template <int ITEMS>
+__device__ __forceinline__ uint32_t valid_items(int cnt, int tid) {
+    const int nvalid = cnt - tid * ITEMS;
+    return nvalid <= 0 ? 0u : (nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u));
+}
+
+// Segment heads of rows of `cols` elements.  Forward: a head is a row's first
+// element (physical index % cols == 0).  Reverse: logical item L is physical
+// tb + cnt - 1 - L and a head is a row's last element.
+template <int ITEMS, bool REVERSE>
+__device__ __forceinline__ uint32_t row_heads(int64_t tb, int cnt, int64_t cols, int tid) {
+    uint32_t hm = 0;
+    if constexpr (!REVERSE) {
+        int64_t r = (tb + static_cast<int64_t>(tid) * ITEMS) % cols;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (r == 0) hm |= 1u << j;
+            r = (r + 1 == cols) ? 0 : r + 1;
+        }
+    } else {
+        int64_t q = (tb + cnt - static_cast<int64_t>(tid) * ITEMS) % cols;
+        if (q < 0) q += cols;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (q == 0) hm |= 1u << j;
+            q = (q == 0) ? cols - 1 : q - 1;
+        }
+    }
+    return hm;
+}
+
+// Sequential reduction of the thread's items; a head restarts the sum.
+template <class Op, int ITEMS, int HEADS>
+__device__ __forceinline__ void thread_reduce(const typename Op::T (&x)[ITEMS], uint32_t hm,
+                                              bool& f, typename Op::Acc& v) {
+    f = false;
+    v = Op::identity();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        if (HEADS != kNoHeads && ((hm >> j) & 1u)) {
+            v = Op::lift(x[j]);
+            f = true;
+        } else {
+            Op::accumulate(v, x[j]);
+        }
+    }
+}
+
+// Inclusive Hillis-Steele scan over the 32 lanes (log2(32) = 5 shift-and-add
+// steps, the in-register scan of Section 3.1 with lanes for SIMD slots).
+template <class Op, int HEADS>
+__device__ __forceinline__ void warp_inclusive_scan(bool& f, typename Op::Acc& v, int lane) {
+    using Acc = typename Op::Acc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const bool fo = __shfl_up_sync(0xffffffffu, f ? 1 : 0, d) != 0;
+        const Acc vo = shfl_up_acc<Op>(v, d);
+        if (lane >= d) {
+            if (HEADS != kNoHeads)
+                seg_combine<Op>(fo, vo, f, v);
+            else
+                v = Op::combine(vo, v);
+        }
+    }
+}
+
+// Outputs of the thread's items given everything before its first item
+// (gf, gv).  Inclusive: y_j = prefix through item j; exclusive: before item j
+// (a segment head starts at 0).  Each output is the carry combined once with
+// the thread's local running sum.
+template <class Op, int ITEMS, int HEADS>
+__device__ __forceinline__ void thread_outputs(const typename Op::T (&x)[ITEMS], uint32_t hm,
+                                               typename Op::Acc gv, bool excl,
+                                               typename Op::T (&y)[ITEMS]) {
+    using T = typename Op::T;
+    using Acc = typename Op::Acc;
+    bool rf = false;
+    Acc rv = Op::identity();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const bool h = HEADS != kNoHeads && ((hm >> j) & 1u);
+        if (excl) {
+            if (h)
+                y[j] = T(0);
+            else if (rf)
+                y[j] = Op::output1(rv);
+            else
+                y[j] = Op::output(gv, rv);
+        }
+        if (h) {
+            rv = Op::lift(x[j]);
+            rf = true;
+        } else {
+            Op::accumulate(rv, x[j]);
+        }
+        if (!excl) y[j] = rf ? Op::output1(rv) : Op::output(gv, rv);
+    }
+}
+
+template <int NTHREADS>
+__device__ __forceinline__ void named_barrier_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NTHREADS) : "memory");
+}
+
+// Bounded mbarrier wait; returns false if the phase did not complete within
+// the limit (or, with epoch != 0, once the launch has been aborted by another
+// wait).  With `report`, a wait that runs out records a timeout for `epoch`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns, Header* hdr, uint32_t epoch,
+                                                  bool report) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    uint32_t polls = 0;
+    while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
+        if ((++polls & 7) == 0 && epoch != 0 && launch_aborted(hdr, epoch)) return false;
+        if (global_timer_ns() - t0 > limit_ns) {
+            if (report) {
+                if (epoch != 0)
+                    record_timeout(hdr, epoch, -1);
+                else
+                    record_error(hdr, GBSCAN_ERR_TIMEOUT, -1);
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
+// Warp-uniform bounded wait: lane 0 alone observes the mbarrier phase (with
+// the bound), the warp learns the outcome, and __syncwarp orders lane 0's
+// view of memory (including the bulk-copied data the phase covers) before the
+// other lanes' accesses.  Only one thread per warp touches the mbarrier:
+// redundant waits by every lane would park the other lanes in the barrier
+// unit for about a microsecond.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                          Header* hdr, uint32_t epoch, int lane) {
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait_bounded(bar, parity, limit_ns, hdr, epoch, true) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+}  // namespace gbscan

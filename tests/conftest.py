@@ -38,3 +38,17 @@ def read_golden(name):
             key, vals = line.split(":", 1)
             out[key.strip()] = [int(v) for v in vals.split()]
     return out
+
+
+@pytest.fixture(autouse=True)
+def _no_device_error_left(request):
+    """After every GPU test, the default workspace of the current stream must
+    hold no device-side error (tests that provoke one read and clear it)."""
+    yield
+    if "gpu" not in request.keywords:
+        return
+    import torch
+    if not torch.cuda.is_available():
+        return
+    import paper_2312_14874_gb300 as gb
+    assert gb.device_status() == 0, "a device-side error was left in the workspace"

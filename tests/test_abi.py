@@ -48,8 +48,10 @@ def test_workspace_size():
     out = ctypes.c_size_t(0)
     L = _capi.lib()
     assert L.gbscan_workspace_size(_capi.I32, _capi.KIND_SCAN, 1 << 30, 0, ctypes.byref(out)) == 0
-    # header + one 32-byte record per smallest tile (+1)
-    assert out.value == 256 + 32 * ((1 << 30) // 3072 + 1 + 1)
+    # header + 512-byte blocks of 16 tile records, one record per smallest
+    # tile (3072 elements) plus one
+    records = -(-(1 << 30) // 3072) + 1
+    assert out.value == 256 + 512 * (-(-records // 16))
     assert L.gbscan_workspace_size(_capi.I32, _capi.KIND_SCAN, -1, 0, ctypes.byref(out)) == \
         _capi.ERR_INVALID_ARG
     assert L.gbscan_workspace_size(9, _capi.KIND_SCAN, 10, 0, ctypes.byref(out)) == \
@@ -108,7 +110,8 @@ def test_variant_table():
         for v in range(nv):
             assert L.gbscan_variant_info(dt, _capi.KIND_SCAN, v, ctypes.byref(t), ctypes.byref(i),
                                          ctypes.byref(s), ctypes.byref(tile)) == 0
-            assert tile.value == t.value * i.value
+            # threads counts the loader warp and one agent warp per stage
+            assert tile.value == (t.value - 32 * (1 + s.value)) * i.value
             esz = 8 if dt in (_capi.I64, _capi.F64) else 4
             assert (i.value * esz) % 16 == 0
             assert ((i.value * esz) // 16) % 2 == 1  # odd vectors: conflict-free LDS.128

@@ -36,10 +36,11 @@ def test_race_stress_random_publication_delays():
     x = to_dev(a)
     ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_SCAN, n))
     gb.set_debug(delay_ns_max=3000, workspace=ws)
-    for rep in range(30):
+    for rep in range(40):
         v = rep % gb.num_variants(torch.int32)
         y = gb.inclusive(x, variant=v, workspace=ws).cpu().numpy()
-        assert np.array_equal(y, want), rep
+        assert gb.device_status(ws) == 0, (rep, v)
+        assert np.array_equal(y, want), (rep, v)
     gb.set_debug(workspace=ws)
     assert gb.device_status(ws) == 0
 
@@ -55,9 +56,14 @@ def test_race_stress_segmented_and_i64():
     b = synth.uniform_i64(n, 1 << 32, seed=4)
     want64 = oracle.scan_i64(b)
     xb = to_dev(b)
-    for rep in range(10):
-        assert np.array_equal(gb.segmented(x, o, exclusive=True, workspace=ws).cpu().numpy(), want)
-        assert np.array_equal(gb.inclusive(xb, workspace=ws).cpu().numpy(), want64)
+    for rep in range(15):
+        v = rep % 3
+        assert np.array_equal(gb.segmented(x, o, exclusive=True, workspace=ws, variant=v)
+                              .cpu().numpy(), want), rep
+        assert gb.device_status(ws) == 0, rep
+        assert np.array_equal(gb.inclusive(xb, workspace=ws, variant=rep % 5).cpu().numpy(),
+                              want64), rep
+        assert gb.device_status(ws) == 0, rep
     gb.set_debug(workspace=ws)
     assert gb.device_status(ws) == 0
 
