@@ -198,6 +198,37 @@ gbscan_status gbscan_copy(const void* src, void* dst, size_t bytes, cudaStream_t
 const char* gbscan_status_string(gbscan_status status);
 int gbscan_abi_version(void);
 
+/*
+ * Inclusive int32 scan that allocates nothing and takes no workspace (the
+ * paper has no counterpart: this is a calling convention, not part of the
+ * method).  It is for callers that cannot allocate device memory: code that
+ * runs where cudaMalloc is forbidden or unavailable, such as inside a
+ * fixed-budget memory pool that must not grow, an allocator callback or a
+ * memory-accounting hook, or an embedding that hands out only the input and
+ * output buffers.
+ *
+ * It runs the same single-pass kernel as scan_inclusive_i32 (default launch
+ * shape), with its scratch (the tile status records) in a library-owned
+ * static device array of GBSCAN_NOALLOC_SCRATCH_BYTES (8 MiB), which every GPU
+ * that loads the library holds until the process exits.  That bounds n at
+ * GBSCAN_NOALLOC_MAX_N elements; larger n returns GBSCAN_ERR_UNSUPPORTED and
+ * launches nothing.
+ *   in, out : device arrays of n int32 (out == in allowed), owned by the caller.
+ *   n       : 0 <= n <= GBSCAN_NOALLOC_MAX_N; n == 0 is a no-op.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call clears the array's launch counters and error
+ * word (cudaMemsetAsync on `stream`), so device-side errors (bounded waits
+ * that ran out) are not reported by this entry point.  All calls share the one
+ * array: calls whose executions overlap on the GPU (other streams, or other
+ * host threads) race and give wrong results; issue them on one stream, or
+ * order them.  No cudaMalloc, cudaFree or allocating library call is made.
+ */
+#define GBSCAN_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define GBSCAN_NOALLOC_MAX_N ((int64_t)1340000000)
+gbscan_status scan_inclusive_i32_noalloc(const int32_t* in, int32_t* out, int64_t n,
+                                         cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,7 @@ _SIGNATURES = {
     "gbscan_copy": [_vp, _vp, _sz, _vp],
     "gbscan_status_string": [_i32],
     "gbscan_abi_version": [],
+    "scan_inclusive_i32_noalloc": [_vp, _vp, _i64, _vp],
 }
 _RESTYPE = {"gbscan_status_string": ctypes.c_char_p, "gbscan_num_variants": ctypes.c_int,
             "gbscan_abi_version": ctypes.c_int}

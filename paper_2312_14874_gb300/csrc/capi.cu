@@ -234,6 +234,11 @@ const Family* family_for(gbscan_dtype dt, gbscan_kind kind) {
 }
 
 }  // namespace
+// Scratch of scan_inclusive_i32_noalloc: a header and tile records for up to
+// GBSCAN_NOALLOC_MAX_N elements at the default int32 tile.  Zero at module
+// load, like a zeroed workspace.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GBSCAN_NOALLOC_SCRATCH_BYTES];
+
 }  // namespace gbscan
 
 using namespace gbscan;
@@ -412,5 +417,44 @@ const char* gbscan_status_string(gbscan_status status) {
 }
 
 int gbscan_abi_version(void) { return GBSCAN_ABI_VERSION; }
+
+// The device address of the static scratch array differs per device; it is
+// looked up once per device (with that device current) and cached.  In host
+// code the array's name is only a host-side stand-in, never passed to a kernel.
+static void* noalloc_scratch_address(int device) {
+    static std::atomic<void*> cache[64];
+    if (device < 0 || device >= 64) return nullptr;
+    void* p = cache[device].load(std::memory_order_acquire);
+    if (p) return p;
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || addr == nullptr) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cache[device].store(addr, std::memory_order_release);
+    return addr;
+}
+
+gbscan_status scan_inclusive_i32_noalloc(const int32_t* in, int32_t* out, int64_t n,
+                                         cudaStream_t stream) {
+    if (n < 0) return GBSCAN_ERR_INVALID_ARG;
+    if (n > GBSCAN_NOALLOC_MAX_N) return GBSCAN_ERR_UNSUPPORTED;
+    if (n == 0) return GBSCAN_OK;
+    const Family& fam = family_scan_i32();
+    const int64_t records = records_for(n, fam.variants[0].tile);
+    if (kHeaderBytes + record_bytes(records) > GBSCAN_NOALLOC_SCRATCH_BYTES)
+        return GBSCAN_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GBSCAN_ERR_CUDA;
+    void* ws = noalloc_scratch_address(dev);
+    if (ws == nullptr) return GBSCAN_ERR_CUDA;
+    // Launch state that must start at zero: the tile and done counters and the
+    // error word (header bytes 4..15).  The epoch (bytes 0..3) is kept: it is
+    // what makes the status records of earlier calls stale.
+    if (cudaMemsetAsync(static_cast<unsigned char*>(ws) + 4, 0, 12, stream) != cudaSuccess)
+        return GBSCAN_ERR_CUDA;
+    return scan_flat(fam, in, out, n, sizeof(int32_t), 0, ws, GBSCAN_NOALLOC_SCRATCH_BYTES,
+                     GBSCAN_ALGO_SINGLE_PASS, 0, stream);
+}
 
 }  // extern "C"
