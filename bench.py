@@ -53,6 +53,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-side", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--algo", choices=["auto", "single_pass", "two_pass", "partitioned"],
+                    default="single_pass", help="scan algorithm of the timed step")
     ap.add_argument("--n-log2", type=int, default=N_LOG2,
                     help="array size 2^k (profiling runs use a smaller case; the benchmark "
                          "workload is 2^30)")
@@ -280,6 +282,8 @@ def side_measurements(dev, peak) -> dict:
     rec("i32_2^30_exclusive", 8 * N, cuda_time_ms(lambda: gb.exclusive(x, out=y, workspace=ws), reps)[0])
     rec("i32_2^30_two_pass", 8 * N, cuda_time_ms(
         lambda: gb.inclusive(x, out=y, workspace=ws, algo="two_pass"), reps)[0])
+    rec("i32_2^30_partitioned", 8 * N, cuda_time_ms(
+        lambda: gb.inclusive(x, out=y, workspace=ws, algo="partitioned"), reps)[0])
     rec("copy_torch_4GiB", 8 * N, cuda_time_ms(lambda: y.copy_(x), reps)[0])
     rec("copy_gbscan_4GiB", 8 * N, cuda_time_ms(lambda: gb.copy_(y, x), reps)[0])
     for v in range(gb.num_variants(torch.int32)):
@@ -293,6 +297,8 @@ def side_measurements(dev, peak) -> dict:
     rec("i64_2^29_single_pass", 16 * n64, cuda_time_ms(lambda: gb.inclusive(x, out=y, workspace=ws), reps)[0])
     rec("i64_2^29_two_pass", 16 * n64, cuda_time_ms(
         lambda: gb.inclusive(x, out=y, workspace=ws, algo="two_pass"), reps)[0])
+    rec("i64_2^29_partitioned", 16 * n64, cuda_time_ms(
+        lambda: gb.inclusive(x, out=y, workspace=ws, algo="partitioned"), reps)[0])
     del x, y
     # fp32 2^28, plain and compensated
     nf = 1 << 28
@@ -301,6 +307,11 @@ def side_measurements(dev, peak) -> dict:
     rec("f32_2^28_plain", 8 * nf, cuda_time_ms(lambda: gb.inclusive(x, out=y, workspace=ws), reps)[0])
     rec("f32_2^28_compensated", 8 * nf, cuda_time_ms(
         lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True), reps)[0])
+    rec("f32_2^28_partitioned", 8 * nf, cuda_time_ms(
+        lambda: gb.inclusive(x, out=y, workspace=ws, algo="partitioned"), reps)[0])
+    rec("f32_2^28_compensated_partitioned", 8 * nf, cuda_time_ms(
+        lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True, algo="partitioned"),
+        reps)[0])
     del x, y
     # segmented: 65,536 log-uniform segments in [1, 2^16], exclusive, CUDA graph
     off = synth.segment_offsets(65536, max_log2=16, seed=0)
@@ -368,7 +379,7 @@ def main(argv=None) -> int:
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        gb.inclusive(x, out=y, workspace=ws, variant=variant)
+        gb.inclusive(x, out=y, workspace=ws, variant=variant, algo=args.algo)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -392,6 +403,7 @@ def main(argv=None) -> int:
     torch.cuda.synchronize(dev)
     barrier(dev)
     clk = clocks.stop()
+    dev_status = gb.device_status(ws, dev)  # 0: no bounded wait ran out
     total_ms = starts[0].elapsed_time(ends[-1])
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     avg_launch_ms = sum(launch_ms) / len(launch_ms)
@@ -409,7 +421,7 @@ def main(argv=None) -> int:
 
         def e2e_step():
             x.copy_(h_in, non_blocking=True)
-            gb.inclusive(x, out=y, workspace=ws, variant=variant)
+            gb.inclusive(x, out=y, workspace=ws, variant=variant, algo=args.algo)
             h_out.copy_(y, non_blocking=True)
 
         e2e_step()
@@ -456,7 +468,7 @@ def main(argv=None) -> int:
             "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "dtype": "int32", "values": "uniform [0,255]",
-                       "algo": "single_pass", "variant": variant, **vinfo,
+                       "algo": args.algo, "variant": variant, **vinfo,
                        "l2": "inputs and outputs 4 GiB each, larger than the 129 MB L2: no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -466,6 +478,7 @@ def main(argv=None) -> int:
                          "avg_launch_ms": round(avg_launch_ms, 4)},
             "e2e": e2e,
             "gpu_launches": args.steps,
+            "device_status": dev_status,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"],
                        "power_w_max": clk.get("power_w_max")},

@@ -62,7 +62,9 @@ typedef enum {
 typedef enum {
     GBSCAN_ALGO_AUTO = 0,        /* the single-pass scan */
     GBSCAN_ALGO_SINGLE_PASS = 1, /* chained scan with decoupled look-back */
-    GBSCAN_ALGO_TWO_PASS = 2     /* reduce tiles, scan the tile sums, scan with offsets */
+    GBSCAN_ALGO_TWO_PASS = 2,    /* reduce tiles, scan the tile sums, scan with offsets */
+    GBSCAN_ALGO_PARTITIONED = 3  /* cache-friendly partitioned two-pass (Section 2.2):
+                                    per L2-sized chunk, reduce then scan from L2, one launch */
 } gbscan_algo;
 
 typedef enum {
@@ -94,8 +96,13 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
  *   in, out   : device arrays of n elements (out == in allowed).
  *   n         : element count, >= 0.
  *   ws        : zeroed workspace of ws_bytes >= gbscan_workspace_size(dtype, SCAN, n, 0).
- *   algo      : GBSCAN_ALGO_AUTO / SINGLE_PASS (one launch) or TWO_PASS (three launches:
- *               tile reduce, one-block scan of the tile sums, scan with offsets).
+ *   algo      : GBSCAN_ALGO_AUTO / SINGLE_PASS (one launch), TWO_PASS (three launches:
+ *               tile reduce, one-block scan of the tile sums, scan with offsets), or
+ *               PARTITIONED (one launch: the array is cut into chunks of about 24 MiB
+ *               (environment variable GBSCAN_CHUNK_BYTES overrides); each chunk is
+ *               reduced tile by tile, its tile sums are scanned, and it is scanned a
+ *               second time while still in L2, overlapped with the reduction of the
+ *               chunk two ahead).
  *   variant   : launch shape (threads, items per thread, pipeline stages), 0 = default;
  *               see gbscan_num_variants / gbscan_variant_info.
  *   mode      : (f32 only) plain fp32 or compensated two-sum carries.

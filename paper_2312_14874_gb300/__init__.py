@@ -38,7 +38,7 @@ _DTYPES = {
     torch.float64: (_capi.F64, "f64"),
 }
 _ALGOS = {"auto": _capi.ALGO_AUTO, "single_pass": _capi.ALGO_SINGLE_PASS,
-          "two_pass": _capi.ALGO_TWO_PASS}
+          "two_pass": _capi.ALGO_TWO_PASS, "partitioned": _capi.ALGO_PARTITIONED}
 
 
 def _stream_handle(device) -> int:

@@ -24,7 +24,7 @@ STATUS_NAMES = {
     ERR_UNSUPPORTED: "GBSCAN_ERR_UNSUPPORTED",
 }
 # gbscan_algo
-ALGO_AUTO, ALGO_SINGLE_PASS, ALGO_TWO_PASS = 0, 1, 2
+ALGO_AUTO, ALGO_SINGLE_PASS, ALGO_TWO_PASS, ALGO_PARTITIONED = 0, 1, 2, 3
 # gbscan_f32_mode
 F32_PLAIN, F32_COMPENSATED = 0, 1
 # gbscan_dtype

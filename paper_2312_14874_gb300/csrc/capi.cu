@@ -2,6 +2,7 @@
 // layout, and dispatch to the tile kernels.  Host code plus three small
 // kernels (segment locator, debug-field writer, copy reference).
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "gbscan_launch.cuh"
@@ -128,11 +129,33 @@ Params make_params(const void* in, void* out, int64_t n, int tile, void* ws, siz
     return p;
 }
 
+// Tiles per chunk of the partitioned scan: about GBSCAN_CHUNK_BYTES of input
+// (default 24 MiB: with the two-chunk lag, two chunks waiting for their second
+// pass and one being reduced, 72 MiB, fit in the 129 MB L2 with room for the
+// streaming stores), within [16, the kernel's limit].
+int64_t partition_chunk_tiles(const Variant& v, size_t esz) {
+    static std::atomic<long long> bytes_cache{0};
+    long long bytes = bytes_cache.load(std::memory_order_relaxed);
+    if (bytes == 0) {
+        bytes = 24ll << 20;
+        if (const char* e = getenv("GBSCAN_CHUNK_BYTES")) {
+            const long long b = atoll(e);
+            if (b > 0) bytes = b;
+        }
+        bytes_cache.store(bytes, std::memory_order_relaxed);
+    }
+    int64_t k = bytes / (static_cast<long long>(v.tile) * static_cast<long long>(esz));
+    if (k < kGroup) k = kGroup;
+    if (k > v.max_chunk_tiles) k = v.max_chunk_tiles;
+    return k;
+}
+
 gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n, size_t esz,
                         int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                         cudaStream_t stream) {
     if (n < 0) return GBSCAN_ERR_INVALID_ARG;
-    if (algo != GBSCAN_ALGO_AUTO && algo != GBSCAN_ALGO_SINGLE_PASS && algo != GBSCAN_ALGO_TWO_PASS)
+    if (algo != GBSCAN_ALGO_AUTO && algo != GBSCAN_ALGO_SINGLE_PASS &&
+        algo != GBSCAN_ALGO_TWO_PASS && algo != GBSCAN_ALGO_PARTITIONED)
         return GBSCAN_ERR_INVALID_ARG;
     if (variant < 0 || variant >= fam.num_variants) return GBSCAN_ERR_INVALID_ARG;
     if (n == 0) return GBSCAN_OK;
@@ -146,6 +169,11 @@ gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n,
     Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
     p.exclusive = exclusive;
     cudaGetLastError();  // clear a stale, non-sticky error of an earlier call
+    if (algo == GBSCAN_ALGO_PARTITIONED) {
+        if (!v.partitioned) return GBSCAN_ERR_UNSUPPORTED;
+        p.chunk_tiles = partition_chunk_tiles(v, esz);
+        return from_cuda(v.partitioned(p, stream));
+    }
     if (algo == GBSCAN_ALGO_TWO_PASS) {
         if (!v.reduce || !v.scan_offset || !fam.scan_sums) return GBSCAN_ERR_UNSUPPORTED;
         cudaError_t e = v.reduce(p, stream);

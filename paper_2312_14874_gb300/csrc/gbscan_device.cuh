@@ -66,7 +66,8 @@ static_assert(sizeof(Header) == 256, "header size");
 //   hi[16]  words 16..31 : 8-byte accumulators only: second status word
 //   aux[16] words 32..47 : two-pass tile sums, or the first segment of the tile
 //   glo, ghi words 48, 49 : status words of the group (the block's 16 tiles)
-//   words 50..63          : unused
+//   words 50..53          : partitioned scan: chunk prefixes (see rec_chunk)
+//   words 54..63          : unused
 // A status word holds
 //   bits 0..31  the value (4-byte accumulators), or one 32-bit half of an
 //               8-byte accumulator (lo: bits 0..31, hi: bits 32..63)
@@ -91,6 +92,12 @@ __device__ __forceinline__ unsigned long long* rec_hi(unsigned long long* rec, i
 }
 __device__ __forceinline__ unsigned long long* rec_aux(unsigned long long* rec, int64_t t) {
     return rec + (t >> 4) * kRecBlockWords + 32 + (t & 15);
+}
+// Partitioned scan: chunk c keeps two status pairs in the spare words of
+// block c: its exclusive prefix E (words 50, 51) and inclusive prefix P
+// (words 52, 53).  A chunk has at least 16 tiles, so block c always exists.
+__device__ __forceinline__ unsigned long long* rec_chunk(unsigned long long* rec, int64_t c, int w) {
+    return rec + c * kRecBlockWords + 50 + w;
 }
 __device__ __forceinline__ unsigned long long* rec_glo(unsigned long long* rec, int64_t g) {
     return rec + g * kRecBlockWords + 48;
@@ -118,6 +125,7 @@ struct Params {
     const int64_t* offsets; // segmented: CSR offsets (num_segments + 1)
     int64_t num_segments;
     int64_t cols;           // row kinds: row length
+    int64_t chunk_tiles;    // partitioned scan: tiles per chunk
     int exclusive;
     int fast;               // in and out are 16-byte aligned: TMA path for full tiles
 };
@@ -183,6 +191,35 @@ __device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint3
         : "memory");
 }
 
+// L2 eviction-priority policies for the bulk copies: keep (data that will be
+// read again soon) or drop first (data read or written for the last time).
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void bulk_load_hint(void* dst_smem, const void* src, uint32_t bytes,
+                                               uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_store_hint(void* dst, const void* src_smem, uint32_t bytes,
+                                                uint64_t policy) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+                 "r"(smem_addr(src_smem)), "r"(bytes), "l"(policy)
+                 : "memory");
+}
+
 // Shared -> global bulk copy, tracked as a bulk group.
 __device__ __forceinline__ void bulk_store(void* dst, const void* src_smem, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
@@ -237,6 +274,10 @@ __device__ __forceinline__ unsigned long long ld_poll_u64(const unsigned long lo
     unsigned long long v;
     asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __device__ __forceinline__ void poll_round_fence() {
@@ -446,13 +487,11 @@ __device__ __forceinline__ void publish_words(unsigned long long* lo, unsigned l
     }
 }
 
+// Decodes a status word pair already in registers (see read_words).
 template <class Op>
-__device__ __forceinline__ void read_words(const unsigned long long* lo, const unsigned long long* hi,
-                                           uint32_t epoch, uint32_t& state, bool& head,
-                                           typename Op::Acc& v) {
-    const unsigned long long w0 = ld_poll_u64(lo);
-    unsigned long long w1 = 0;
-    if constexpr (!Op::kPacked) w1 = ld_poll_u64(hi);
+__device__ __forceinline__ void parse_words(unsigned long long w0, unsigned long long w1,
+                                            uint32_t epoch, uint32_t& state, bool& head,
+                                            typename Op::Acc& v) {
     const uint32_t meta = static_cast<uint32_t>(w0 >> 32);
     bool ok = (meta >> 3) == epoch;
     if constexpr (!Op::kPacked) ok = ok && static_cast<uint32_t>(w1 >> 32) == meta;
@@ -468,6 +507,18 @@ __device__ __forceinline__ void read_words(const unsigned long long* lo, const u
         v = Op::from_bits(static_cast<typename Op::Bits>(w0 & 0xffffffffull));
     else
         v = Op::from_bits(static_cast<typename Op::Bits>((w1 << 32) | (w0 & 0xffffffffull)));
+}
+
+// Polls a status word pair in global memory: state X when the pair is not a
+// publication of this launch (stale epoch, or halves from two publications).
+template <class Op>
+__device__ __forceinline__ void read_words(const unsigned long long* lo, const unsigned long long* hi,
+                                           uint32_t epoch, uint32_t& state, bool& head,
+                                           typename Op::Acc& v) {
+    const unsigned long long w0 = ld_poll_u64(lo);
+    unsigned long long w1 = 0;
+    if constexpr (!Op::kPacked) w1 = ld_poll_u64(hi);
+    parse_words<Op>(w0, w1, epoch, state, head, v);
 }
 
 template <class Op>
@@ -744,6 +795,23 @@ __device__ __forceinline__ bool finish_launch(Header* hdr, uint32_t epoch) {
     hdr->epoch = wrap ? 0u : epoch;
     if (wrap) hdr->abort_epoch = 0u;
     return wrap;
+}
+
+// Zero every status word of `capacity` tile records (tile, group and chunk
+// words), by `nthreads` threads of one block.
+__device__ __forceinline__ void clear_status_words(unsigned long long* rec, int64_t capacity,
+                                                   int tid, int nthreads) {
+    for (int64_t i = tid; i < capacity; i += nthreads) {
+        *rec_lo(rec, i) = 0ull;
+        *rec_hi(rec, i) = 0ull;
+        if (i % kGroup == 0) {
+            const int64_t b = i / kGroup;
+            *rec_glo(rec, b) = 0ull;
+            *rec_ghi(rec, b) = 0ull;
+            for (int w = 0; w < 4; ++w) *rec_chunk(rec, b, w) = 0ull;
+        }
+    }
+    __threadfence();
 }
 
 __device__ __forceinline__ uint32_t launch_epoch(uint32_t completed) {

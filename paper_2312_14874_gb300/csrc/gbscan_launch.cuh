@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "partitioned.cuh"
 
 namespace gbscan {
 
@@ -18,6 +19,8 @@ struct Variant {
     LaunchFn single_pass;  // chained scan with decoupled look-back
     LaunchFn reduce;       // two-pass: tile sums (null where not built)
     LaunchFn scan_offset;  // two-pass: scan with the scanned tile sums
+    LaunchFn partitioned;  // cache-friendly partitioned scan (null where not built)
+    int max_chunk_tiles;   // partitioned: most tiles a chunk may have
 };
 
 struct Family {
@@ -70,6 +73,14 @@ cudaError_t launch_tp(const Params& p, cudaStream_t stream) {
                              tp_smem_bytes<Op, THREADS, ITEMS, STAGES>(), occ_cache, p, stream);
 }
 
+template <class Op, int CWARPS, int ITEMS, int STAGES, int MINB>
+cudaError_t launch_pt(const Params& p, cudaStream_t stream) {
+    static std::atomic<int> occ_cache[64];
+    return launch_persistent(partitioned_kernel<Op, CWARPS, ITEMS, STAGES, MINB>,
+                             pt_threads<CWARPS>(), pt_smem_bytes<Op, CWARPS, ITEMS, STAGES>(),
+                             occ_cache, p, stream);
+}
+
 template <class Op>
 cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStream_t stream) {
     scan_tile_sums_kernel<Op, 1024><<<1, 1024, 0, stream>>>(rec, num_tiles);
@@ -85,12 +96,13 @@ cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStr
 #define GBSCAN_VARIANT_SP(OP, CW, I, S, LB, MB, HEADS_, REV_)                                   \
     Variant {                                                                                  \
         (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, HEADS_, REV_, LB, MB>, nullptr, \
-            nullptr                                                                            \
+            nullptr, nullptr, 0                                                                \
     }
 #define GBSCAN_VARIANT_ALL(OP, CW, I, S, LB, MB, TS)                                          \
     Variant {                                                                                 \
         (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, kNoHeads, false, LB, MB>, \
-            &launch_tp<OP, CW * 32, I, TS, kReduce>, &launch_tp<OP, CW * 32, I, TS, kScanOffset> \
+            &launch_tp<OP, CW * 32, I, TS, kReduce>, &launch_tp<OP, CW * 32, I, TS, kScanOffset>, \
+            &launch_pt<OP, CW, I, (S > 2 ? S : 3), (MB > 2 ? 2 : MB)>, CW * 32 * kChunkPerThread     \
     }
 
 // Families, one per translation unit group.

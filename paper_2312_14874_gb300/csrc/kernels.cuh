@@ -382,17 +382,7 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
         c.clear = finish_launch(hdr, epoch) ? 1u : 0u;
     }
     __syncthreads();
-    if (c.clear) {
-        for (int64_t i = tid; i < p.rec_capacity; i += blockDim.x) {
-            *rec_lo(p.rec, i) = 0ull;
-            *rec_hi(p.rec, i) = 0ull;
-            if (i % kGroup == 0) {
-                *rec_glo(p.rec, i / kGroup) = 0ull;
-                *rec_ghi(p.rec, i / kGroup) = 0ull;
-            }
-        }
-        __threadfence();
-    }
+    if (c.clear) clear_status_words(p.rec, p.rec_capacity, tid, blockDim.x);
 }
 
 // ---------------------------------------------------------------------------

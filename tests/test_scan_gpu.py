@@ -65,7 +65,7 @@ def check(dtype_key, a, y, excl, compensated=False):
 
 
 @pytest.mark.parametrize("dtype_key", ["i32", "i64", "f32", "f64"])
-@pytest.mark.parametrize("algo", ["single_pass", "two_pass"])
+@pytest.mark.parametrize("algo", ["single_pass", "two_pass", "partitioned"])
 def test_scan_sizes_all_variants(dtype_key, algo):
     torch_dt = {"i32": torch.int32, "i64": torch.int64, "f32": torch.float32,
                 "f64": torch.float64}[dtype_key]
@@ -79,7 +79,7 @@ def test_scan_sizes_all_variants(dtype_key, algo):
     assert gb.device_status() == 0
 
 
-@pytest.mark.parametrize("algo", ["single_pass", "two_pass"])
+@pytest.mark.parametrize("algo", ["single_pass", "two_pass", "partitioned"])
 def test_scan_f32_compensated(algo):
     for v in variants(torch.float32):
         for n in SIZES:
@@ -109,7 +109,7 @@ def test_closed_forms_on_gpu():
 def test_in_place(dtype_key):
     n = 5 * 5120 + 13
     a = gen(dtype_key, n, seed=7)
-    for algo in ("single_pass", "two_pass"):
+    for algo in ("single_pass", "two_pass", "partitioned"):
         for excl in (False, True):
             x = to_dev(a)
             y = gb.scan(x, excl, out=x, algo=algo)
@@ -154,7 +154,7 @@ def test_canary_guard_zones():
     L = _capi.lib()
     s = torch.cuda.current_stream().cuda_stream
     wptr = wsbuf.data_ptr() + 4096
-    for algo in (1, 2):
+    for algo in (1, 2, 3):
         assert L.scan_inclusive_i32(x.data_ptr(), out.data_ptr(), n, wptr, ws_need, algo, 0, s) == 0
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy(), oracle.scan_i32(a))
@@ -189,3 +189,67 @@ def test_many_launches_reuse_workspace():
         z = gb.exclusive(to_dev(b), workspace=ws).cpu().numpy()
         assert np.array_equal(z, oracle.scan_i64(b, True))
     assert gb.device_status(ws) == 0
+
+
+PARTITION_SCRIPT = r"""
+import sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import oracle, synth
+import paper_2312_14874_gb300 as gb
+dev = torch.device("cuda", 0)
+# 16-tile chunks (the smallest): many chunk boundaries and a ragged last chunk
+for key, n in (("i32", 16 * 5120 * 37 + 99), ("i64", 16 * 2560 * 21 + 5), ("f32", 16 * 5120 * 9 + 7),
+               ("f64", 16 * 2560 * 5 + 3)):
+    for v in range(gb.num_variants({"i32": torch.int32, "i64": torch.int64, "f32": torch.float32,
+                                    "f64": torch.float64}[key])):
+        if key == "i32":
+            a = synth.uniform_i32(n, 1 << 20, seed=v)
+        elif key == "i64":
+            a = synth.uniform_i64(n, 1 << 32, seed=v)
+        elif key == "f32":
+            a = synth.normal_f32(n, seed=v)
+        else:
+            a = synth.normal_f64(n, seed=v)
+        x = torch.from_numpy(a).to(dev)
+        for excl in (False, True):
+            y = gb.scan(x, excl, algo="partitioned", variant=v).cpu().numpy()
+            if key == "i32":
+                assert np.array_equal(y, oracle.scan_i32(a, excl)), (key, v, excl)
+            elif key == "i64":
+                assert np.array_equal(y, oracle.scan_i64(a, excl)), (key, v, excl)
+            elif key == "f32":
+                err, _ = oracle.max_rel_err(y, oracle.scan_f32_ref(a, excl), oracle.abs_scan_f32(a, excl))
+                assert err <= 1e-5, (key, v, excl, err)
+            else:
+                err, _ = oracle.max_rel_err(y, oracle.scan_f64_ref(a, excl),
+                                            oracle.scan_f64_ref(np.abs(a), excl))
+                assert err <= 1e-13, (key, v, excl, err)
+assert gb.device_status() == 0
+print("ok")
+"""
+
+
+def test_partitioned_many_small_chunks(tmp_path):
+    """The partitioned scan with the smallest chunks (16 tiles, set through
+    GBSCAN_CHUNK_BYTES in a child process): dozens of chunk prefixes chained."""
+    import os
+    import subprocess
+    import sys
+    from conftest import ROOT
+    script = tmp_path / "part.py"
+    script.write_text(PARTITION_SCRIPT)
+    env = dict(os.environ, GBSCAN_CHUNK_BYTES="4096")
+    r = subprocess.run([sys.executable, str(script), ROOT], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
+def test_partitioned_multi_chunk_default_size():
+    """Default 32 MiB chunks: an array of several chunks plus a ragged tail."""
+    n = 7 * 1228 * 5120 + 12345
+    a = synth.uniform_i32(n, 256, seed=11)
+    x = to_dev(a)
+    for excl in (False, True):
+        y = gb.scan(x, excl, algo="partitioned").cpu().numpy()
+        assert np.array_equal(y, oracle.scan_i32(a, excl))
