@@ -130,24 +130,38 @@ Params make_params(const void* in, void* out, int64_t n, int tile, void* ws, siz
 }
 
 // Tiles per chunk of the partitioned scan: about GBSCAN_CHUNK_BYTES of input
-// (default 24 MiB: with the two-chunk lag, two chunks waiting for their second
-// pass and one being reduced, 72 MiB, fit in the 129 MB L2 with room for the
-// streaming stores), within [16, the kernel's limit].
+// (default 12 MiB: with the default three-chunk lag, four chunks of input,
+// 48 MiB, are live in the 129 MB L2 at a time, next to the streaming stores),
+// at least 16 tiles.
+static long long env_cached(std::atomic<long long>& cache, const char* name, long long dflt) {
+    long long v = cache.load(std::memory_order_relaxed);
+    if (v == 0) {
+        v = dflt;
+        if (const char* e = getenv(name)) {
+            const long long b = atoll(e);
+            if (b > 0) v = b;
+        }
+        cache.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 int64_t partition_chunk_tiles(const Variant& v, size_t esz) {
     static std::atomic<long long> bytes_cache{0};
-    long long bytes = bytes_cache.load(std::memory_order_relaxed);
-    if (bytes == 0) {
-        bytes = 24ll << 20;
-        if (const char* e = getenv("GBSCAN_CHUNK_BYTES")) {
-            const long long b = atoll(e);
-            if (b > 0) bytes = b;
-        }
-        bytes_cache.store(bytes, std::memory_order_relaxed);
-    }
+    const long long bytes = env_cached(bytes_cache, "GBSCAN_CHUNK_BYTES", 12ll << 20);
     int64_t k = bytes / (static_cast<long long>(v.tile) * static_cast<long long>(esz));
     if (k < kGroup) k = kGroup;
     if (k > v.max_chunk_tiles) k = v.max_chunk_tiles;
     return k;
+}
+
+// Chunks between a chunk's reduction and its scan (GBSCAN_CHUNK_LAG, default 3,
+// at most 8): the slack the chunk scanner has to publish a chunk's offsets
+// before the chunk's second pass starts.
+int64_t partition_chunk_lag() {
+    static std::atomic<long long> lag_cache{0};
+    const long long lag = env_cached(lag_cache, "GBSCAN_CHUNK_LAG", 3);
+    return lag > 8 ? 8 : lag;
 }
 
 gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n, size_t esz,
@@ -172,6 +186,7 @@ gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n,
     if (algo == GBSCAN_ALGO_PARTITIONED) {
         if (!v.partitioned) return GBSCAN_ERR_UNSUPPORTED;
         p.chunk_tiles = partition_chunk_tiles(v, esz);
+        p.chunk_lag = partition_chunk_lag();
         return from_cuda(v.partitioned(p, stream));
     }
     if (algo == GBSCAN_ALGO_TWO_PASS) {

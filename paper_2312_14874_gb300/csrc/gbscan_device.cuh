@@ -126,6 +126,7 @@ struct Params {
     int64_t num_segments;
     int64_t cols;           // row kinds: row length
     int64_t chunk_tiles;    // partitioned scan: tiles per chunk
+    int64_t chunk_lag;      // partitioned scan: chunk c is scanned beside the reduction of c + lag
     int exclusive;
     int fast;               // in and out are 16-byte aligned: TMA path for full tiles
 };
@@ -158,6 +159,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Non-blocking test of the same phase condition: never suspends the thread.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_addr(bar)), "r"(parity)

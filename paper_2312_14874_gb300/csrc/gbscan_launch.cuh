@@ -33,10 +33,11 @@ int device_sm_count(int device);
 
 // Launch a kernel as a persistent grid: one block per resident slot, never
 // more blocks than tiles.  Shared-memory opt-in and occupancy are queried once
-// per device and kernel.
+// per device and kernel.  A cooperative launch guarantees that all blocks are
+// resident at once (or fails), for kernels whose blocks take work statically.
 template <class Kernel>
 cudaError_t launch_persistent(Kernel kern, int threads, int smem, std::atomic<int>* occ_cache,
-                              const Params& p, cudaStream_t stream) {
+                              const Params& p, cudaStream_t stream, bool cooperative = false) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -54,8 +55,21 @@ cudaError_t launch_persistent(Kernel kern, int threads, int smem, std::atomic<in
     int64_t grid = static_cast<int64_t>(sms) * occ;
     if (grid > p.num_tiles) grid = p.num_tiles;
     if (grid < 1) grid = 1;
-    kern<<<static_cast<unsigned>(grid), threads, smem, stream>>>(p);
-    return cudaGetLastError();
+    if (!cooperative) {
+        kern<<<static_cast<unsigned>(grid), threads, smem, stream>>>(p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 template <class Op, int CWARPS, int ITEMS, int STAGES, int HEADS, bool REVERSE, int LB, int MINB>
@@ -102,7 +116,7 @@ cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStr
     Variant {                                                                                 \
         (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, kNoHeads, false, LB, MB>, \
             &launch_tp<OP, CW * 32, I, TS, kReduce>, &launch_tp<OP, CW * 32, I, TS, kScanOffset>, \
-            &launch_pt<OP, CW, I, (S > 2 ? S : 3), (MB > 2 ? 2 : MB)>, CW * 32 * kChunkPerThread     \
+            &launch_pt<OP, CW, I, (S > 2 ? S : 3), (MB > 2 ? 2 : MB)>, kMaxChunkTiles                \
     }
 
 // Families, one per translation unit group.

@@ -8,8 +8,8 @@
 // the GPU's L2 (129 MB): a chunk is a run of chunk_tiles tiles of a few tens of
 // MB, and one persistent launch processes a work list in which the second pass
 // (scan) of chunk c is interleaved with the first pass (reduce, "Accumulate")
-// of chunk c+2 (a lag of two chunks, so that the scan of chunk c's tile sums
-// has a whole chunk of reductions to finish in):
+// of chunk c+lag (by default a lag of two chunks, so that the scan of chunk c's
+// tile sums has a whole slot of work to finish in):
 //
 //   R(0) R(1) | S(0) R(2) S(0) R(2) ... | S(1) R(3) ... | ... | S(C-1)
 //
@@ -36,50 +36,63 @@ namespace gbscan {
 
 enum : uint32_t { kItemReduce = 0, kItemScan = 1 };
 
-constexpr int64_t kLag = 2;  // S(c) is interleaved with R(c + kLag)
+// The constants of the work list for one launch: num_tiles tiles in chunks of
+// K, the scan of chunk c interleaved with the reduction of chunk c + lag
+// (lag >= 1).  Every count fits 32 bits (fewer than 2^31 tiles).
+struct PtOrder {
+    uint32_t K, lag, C, nlast, npre, F;
+};
 
-// Work item w of the list above, for num_tiles tiles in chunks of K:
-//   R(0) .. R(kLag-1) in tile order, then for each chunk c the slot
-//   S(c) / R(c+kLag) alternating (S first) while both have items, then the rest.
-__device__ __forceinline__ void partitioned_item(int64_t w, int64_t num_tiles, int64_t K,
-                                                 uint32_t& phase, int64_t& tile) {
-    const int64_t C = (num_tiles + K - 1) / K;
-    const int64_t nlast = num_tiles - (C - 1) * K;
-    const int64_t pre = kLag < C ? kLag : C;
-    const int64_t npre = pre < C ? pre * K : (C - 1) * K + nlast;
-    if (w < npre) {
+__device__ __forceinline__ PtOrder make_order(int64_t num_tiles, int64_t K, int64_t lag) {
+    PtOrder o;
+    o.K = static_cast<uint32_t>(K);
+    o.lag = static_cast<uint32_t>(lag);
+    o.C = static_cast<uint32_t>((num_tiles + K - 1) / K);
+    o.nlast = static_cast<uint32_t>(num_tiles - static_cast<int64_t>(o.C - 1) * K);
+    const uint32_t pre = o.lag < o.C ? o.lag : o.C;
+    o.npre = pre < o.C ? pre * o.K : (o.C - 1) * o.K + o.nlast;
+    o.F = o.C > o.lag + 1 ? o.C - 1 - o.lag : 0;  // slots with both parts full
+    return o;
+}
+
+// Work item w of the list above:
+//   R(0) .. R(lag-1) in tile order, then for each chunk c the slot
+//   S(c) / R(c+lag) alternating (S first) while both have items, then the rest.
+__device__ __forceinline__ void partitioned_item(uint32_t w, const PtOrder& o, uint32_t& phase,
+                                                 int64_t& tile) {
+    if (w < o.npre) {
         phase = kItemReduce;
         tile = w;
         return;
     }
-    w -= npre;
-    const int64_t F = C - 1 - kLag > 0 ? C - 1 - kLag : 0;  // slots with both parts full
-    if (w < F * 2 * K) {
-        const int64_t c = w / (2 * K), off = w % (2 * K), j = off / 2;
+    w -= o.npre;
+    const uint32_t K2 = 2 * o.K;
+    if (w < o.F * K2) {
+        const uint32_t c = w / K2, off = w - c * K2, j = off >> 1;
         phase = (off & 1) ? kItemReduce : kItemScan;
-        tile = ((off & 1) ? c + kLag : c) * K + j;
+        tile = static_cast<int64_t>((off & 1) ? c + o.lag : c) * o.K + j;
         return;
     }
-    w -= F * 2 * K;
-    int64_t c = F;
-    if (C - 1 - kLag >= 0) {
+    w -= o.F * K2;
+    uint32_t c = o.F;
+    if (o.C >= o.lag + 1) {
         // slot F: S(F) (K items) alternating with R(C-1) (nlast items)
-        if (w < 2 * nlast) {
-            const int64_t j = w / 2;
+        if (w < 2 * o.nlast) {
+            const uint32_t j = w >> 1;
             phase = (w & 1) ? kItemReduce : kItemScan;
-            tile = ((w & 1) ? C - 1 : F) * K + j;
+            tile = static_cast<int64_t>((w & 1) ? o.C - 1 : o.F) * o.K + j;
             return;
         }
-        if (w < K + nlast) {
+        if (w < o.K + o.nlast) {
             phase = kItemScan;
-            tile = F * K + nlast + (w - 2 * nlast);
+            tile = static_cast<int64_t>(o.F) * o.K + o.nlast + (w - 2 * o.nlast);
             return;
         }
-        w -= K + nlast;
-        c = F + 1;
+        w -= o.K + o.nlast;
+        c = o.F + 1;
     }
     phase = kItemScan;  // the remaining slots hold scans only, in tile order
-    tile = c * K + w;
+    tile = static_cast<int64_t>(c) * o.K + w;
 }
 
 template <class Op, int CWARPS, int STAGES, int TILE>
@@ -95,9 +108,13 @@ struct PtCtrl {
     alignas(16) unsigned long long stat[STAGES][6];
     Acc wtot_v[CWARPS];
     Acc prefix_v;
+    uint64_t scan_req;   // consumers -> scanner warp: a chunk to scan (or -1: stop)
+    uint64_t scan_idle;  // scanner warp -> consumers: the request is done
+    int64_t scan_chunk;
     uint32_t epoch;
     uint32_t clear;
     uint32_t cflag;
+    unsigned int claim_sink;
 };
 
 template <class Op, int CWARPS, int ITEMS, int STAGES>
@@ -106,23 +123,152 @@ constexpr int pt_smem_bytes() {
            static_cast<int>(sizeof(PtCtrl<Op, CWARPS, STAGES, CWARPS * 32 * ITEMS>));
 }
 
+// Consumer warps, the loader warp and the chunk scanner warp.
 template <int CWARPS>
 constexpr int pt_threads() {
-    return (CWARPS + 1) * 32;
+    return (CWARPS + 2) * 32;
 }
 
-// Most tiles a chunk may have: the chunk scan gives each consumer thread up to
-// kChunkPerThread tile sums.
-constexpr int kChunkPerThread = 16;
+// Work items a loader claims with one atomic.
+constexpr int kClaim = 2;
+
+// Most tiles a chunk may have.
+constexpr int kMaxChunkTiles = 1 << 16;
+
+// Issues the reads of R status-word rows (32 tiles each, row q of the batch
+// holding tiles r0 + 32q .. r0 + 32q + 31 of the chunk that starts at tile
+// `first`); tiles at or past nch are left as zero words.
+template <class Op, int R>
+__device__ __forceinline__ void chunk_rows_issue(const unsigned long long* rec, int64_t first,
+                                                 int64_t nch, int64_t r0, int lane,
+                                                 unsigned long long (&w0)[R],
+                                                 unsigned long long (&w1)[R]) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int64_t i = r0 + q * 32 + lane;
+        w0[q] = 0ull;
+        w1[q] = 0ull;
+        if (i < nch) {
+            w0[q] = ld_poll_u64(rec_lo(const_cast<unsigned long long*>(rec), first + i));
+            if constexpr (!Op::kPacked)
+                w1[q] = ld_poll_u64(rec_hi(const_cast<unsigned long long*>(rec), first + i));
+        }
+    }
+}
+
+// The scan of one chunk's tile sums (the partition's `sums` array), by one
+// warp: waits until every tile of chunk ch has published its sum, replaces
+// each sum by the tile's exclusive offset within the chunk (state P), then
+// chains the chunk prefixes: E(ch) = P(ch-1) (the sum of all earlier chunks)
+// and P(ch) = E(ch) + the chunk's total.  The sums are read in batches of R
+// rows of 32 consecutive tiles (the next batch's reads go out before the
+// current batch is scanned); the rows of a batch are scanned independently
+// with warp shuffles, and a running carry joins them in the publishing loop.
+template <class Op>
+__device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32_t epoch,
+                                const LookbackCfg& cfg, int lane) {
+    using Acc = typename Op::Acc;
+    constexpr int R = 8;
+    const int64_t K = p.chunk_tiles;
+    const int64_t first = ch * K;
+    const int64_t nch = (p.num_tiles - first) < K ? (p.num_tiles - first) : K;
+    Acc carry = Op::identity();
+    bool ok = true;
+    unsigned long long w0[R], w1[R];
+    chunk_rows_issue<Op, R>(p.rec, first, nch, 0, lane, w0, w1);
+    for (int64_t r0 = 0; r0 < nch; r0 += 32 * R) {
+        Acc v[R];
+        uint32_t st[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            bool hf;
+            v[q] = Op::identity();
+            st[q] = kStateA;  // entries past the chunk count as published
+            if (r0 + q * 32 + lane < nch) parse_words<Op>(w0[q], w1[q], epoch, st[q], hf, v[q]);
+        }
+        if (r0 + 32 * R < nch) chunk_rows_issue<Op, R>(p.rec, first, nch, r0 + 32 * R, lane, w0, w1);
+        const uint64_t t0 = global_timer_ns();
+        while (true) {
+            bool missing = false;
+#pragma unroll
+            for (int q = 0; q < R; ++q) missing |= st[q] == kStateX;
+            if (!missing) break;
+            if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
+                ok = false;
+                break;
+            }
+            __nanosleep(64);
+            poll_round_fence();
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (st[q] == kStateX) {
+                    bool hf;
+                    const int64_t i = first + r0 + q * 32 + lane;
+                    read_words<Op>(rec_lo(p.rec, i), rec_hi(p.rec, i), epoch, st[q], hf, v[q]);
+                }
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        // row scans (independent of one another): ex = exclusive within the
+        // row, v = the row's total
+        Acc ex[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            Acc inc = v[q];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const Acc o = shfl_up_acc<Op>(inc, d);
+                if (lane >= d) inc = Op::combine(o, inc);
+            }
+            ex[q] = shfl_up_acc<Op>(inc, 1);
+            if (lane == 0) ex[q] = Op::identity();
+            v[q] = shfl_idx_acc<Op>(inc, 31);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int64_t i = r0 + q * 32 + lane;
+            // the in-chunk offset replaces the sum (state P)
+            if (i < nch) publish<Op>(p.rec, first + i, epoch, kStateP, false, Op::combine(carry, ex[q]));
+            carry = Op::combine(carry, v[q]);
+        }
+    }
+    if (lane == 0) {
+        if (!ok) {
+            record_timeout(hdr, epoch, first);
+            return;
+        }
+        Acc e = Op::identity();
+        if (ch > 0) {
+            uint32_t st = kStateX;
+            bool hf;
+            const uint64_t t0 = global_timer_ns();
+            while (true) {
+                read_words<Op>(rec_chunk(p.rec, ch - 1, 2), rec_chunk(p.rec, ch - 1, 3), epoch, st, hf, e);
+                if (st == kStateP) break;
+                if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
+                    record_timeout(hdr, epoch, first);
+                    return;
+                }
+                __nanosleep(64);
+                poll_round_fence();
+            }
+        }
+        publish_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, kStateP, false, e);
+        publish_words<Op>(rec_chunk(p.rec, ch, 2), rec_chunk(p.rec, ch, 3), epoch, kStateP, false,
+                          Op::combine(e, carry));
+    }
+}
 
 template <class Op, int CWARPS, int ITEMS, int STAGES, int MINB>
-__global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) partitioned_kernel(const Params p) {
+__global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(const Params p) {
     using T = typename Op::T;
     using Acc = typename Op::Acc;
     constexpr int CTHREADS = CWARPS * 32;
     constexpr int TILE = CTHREADS * ITEMS;
     constexpr int TILE_BYTES = TILE * static_cast<int>(sizeof(T));
     constexpr int LOAD_WARP = CWARPS;
+    constexpr int SCAN_WARP = CWARPS + 1;
     static_assert(STAGES >= 2, "a stage is released one store later: at least two stages");
     using CtrlT = PtCtrl<Op, CWARPS, STAGES, TILE>;
 
@@ -141,6 +287,8 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) partitioned_kernel(co
             mbar_init(&c.full[s], 1);
             mbar_init(&c.empty[s], 1);
         }
+        mbar_init(&c.scan_req, 1);
+        mbar_init(&c.scan_idle, 1);
         fence_mbar_init();
         c.epoch = hdr->epoch;
         c.clear = 0;
@@ -158,14 +306,31 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) partitioned_kernel(co
         const T* __restrict__ in = static_cast<const T*>(p.in);
         const uint64_t keep = l2_policy_evict_last();
         const uint64_t drop = l2_policy_evict_first();
+        // The loader claims kClaim consecutive items per atomic and keeps the
+        // next batch's claim in flight while it issues the current batch, so
+        // that the atomic's round trip (about a microsecond under load) neither
+        // paces the loads (one atomic per item would) nor sits between a stage
+        // coming free and its next load.
+        const PtOrder order = make_order(num_tiles, K, p.chunk_lag);
+        unsigned int cur = 0, nxt = 0;
+        if (lane == 0) {
+            cur = atomicAdd(&hdr->tile_counter, static_cast<unsigned int>(kClaim));
+            nxt = atomicAdd(&hdr->tile_counter, static_cast<unsigned int>(kClaim));
+        }
+        int in_batch = 0;
         for (uint32_t k = 0;; ++k) {
             const int s = static_cast<int>(k % STAGES);
             const uint32_t use = k / STAGES;
             if (use > 0 && !warp_wait(&c.empty[s], (use - 1) & 1u, role_limit, hdr, epoch, lane))
                 break;
-            long long claimed = 0;
-            if (lane == 0) claimed = static_cast<long long>(atomicAdd(&hdr->tile_counter, 1u));
-            const int64_t w = __shfl_sync(0xffffffffu, claimed, 0);
+            const int64_t w = static_cast<int64_t>(__shfl_sync(0xffffffffu, cur, 0)) + in_batch;
+            if (++in_batch == kClaim) {
+                in_batch = 0;
+                if (lane == 0) {
+                    cur = nxt;
+                    nxt = atomicAdd(&hdr->tile_counter, static_cast<unsigned int>(kClaim));
+                }
+            }
             if (w >= num_items) {
                 // end: a sentinel stage ends the consumers' loop
                 if (lane == 0) {
@@ -176,7 +341,7 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) partitioned_kernel(co
             }
             uint32_t phase;
             int64_t t;
-            partitioned_item(w, num_tiles, K, phase, t);
+            partitioned_item(static_cast<uint32_t>(w), order, phase, t);
             const int cnt = count_of(t);
             const bool fast = p.fast && cnt == TILE;
             T* buf = reinterpret_cast<T*>(smem + s * TILE_BYTES);
@@ -200,18 +365,25 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) partitioned_kernel(co
                         // the 16-byte pairs holding the tile's status words, and E
                         unsigned long long* pair = rec_lo(p.rec, t & ~int64_t(1));
                         bulk_load(&c.stat[s][0], pair, 16, &c.full[s]);
-                        bulk_load(&c.stat[s][4], rec_chunk(p.rec, t / K, 0), 16, &c.full[s]);
+                        const uint32_t ch = static_cast<uint32_t>(t) / order.K;
+                        bulk_load(&c.stat[s][4], rec_chunk(p.rec, ch, 0), 16, &c.full[s]);
                         if (!Op::kPacked)
                             bulk_load(&c.stat[s][2], rec_hi(p.rec, t & ~int64_t(1)), 16, &c.full[s]);
                     }
                 }
             }
         }
-    } else {
+        // the claims still in flight must land before this block reports itself
+        // done (the last block to finish resets the counter): the store waits
+        // for the atomics' results
+        if (lane == 0) *static_cast<volatile unsigned int*>(&c.claim_sink) = cur ^ nxt;
+    } else if (warp < CWARPS) {
         T* out = static_cast<T*>(p.out);
         const bool excl = p.exclusive != 0;
         const uint64_t drop = l2_policy_evict_first();
         int pending = -1;
+        uint32_t scan_uses = 0;  // thread 0: requests sent to the scanner warp
+        bool scan_ok = true;
         for (uint32_t k = 0;; ++k) {
             const int s = static_cast<int>(k % STAGES);
             const uint32_t use = k / STAGES;
@@ -256,91 +428,22 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) partitioned_kernel(co
                     publish<Op>(p.rec, t, epoch, kStateA, false, total);
                     mbar_arrive(&c.empty[s]);  // every thread holds its items: stage free
                 }
-                const int64_t ch = t / K;
-                const int64_t first = ch * K;
-                const int64_t nch = (num_tiles - first) < K ? (num_tiles - first) : K;
-                if (t == first + nch - 1) {
-                    // ---- the chunk's sums: in-chunk offsets, chunk prefixes -----
-                    named_barrier_sync<CTHREADS>(1);  // thread 0 has read wtot_v
-                    Acc sv[kChunkPerThread];
-                    const int64_t per = (nch + CTHREADS - 1) / CTHREADS;
-                    const int64_t i0 = first + static_cast<int64_t>(tid) * per;
-                    Acc run = Op::identity();
-                    bool ok = true;
-#pragma unroll
-                    for (int q = 0; q < kChunkPerThread; ++q) {
-                        sv[q] = Op::identity();
-                        const int64_t i = i0 + q;
-                        if (q < per && i < first + nch) {
-                            uint32_t st = kStateX;
-                            bool hf;
-                            const uint64_t t0 = global_timer_ns();
-                            while (true) {
-                                read_words<Op>(rec_lo(p.rec, i), rec_hi(p.rec, i), epoch, st, hf,
-                                               sv[q]);
-                                if (st != kStateX) break;
-                                if (global_timer_ns() - t0 > cfg.spin_limit_ns ||
-                                    launch_aborted(hdr, epoch)) {
-                                    ok = false;
-                                    break;
-                                }
-                                __nanosleep(64);
-                                poll_round_fence();
-                            }
-                            run = Op::combine(run, sv[q]);
+                if (tid == 0) {
+                    const int64_t ch = static_cast<uint32_t>(t) / static_cast<uint32_t>(K);
+                    const int64_t first = ch * K;
+                    const int64_t nch = (num_tiles - first) < K ? (num_tiles - first) : K;
+                    if (t == first + nch - 1) {
+                        // the chunk's last tile: its sums go to the scanner warp,
+                        // and the consumers go on with the next item meanwhile
+                        if (scan_uses > 0 &&
+                            !mbar_wait_bounded(&c.scan_idle, (scan_uses - 1) & 1u, role_limit, hdr, epoch,
+                                               true))
+                            scan_ok = false;
+                        if (scan_ok) {
+                            c.scan_chunk = ch;
+                            mbar_arrive(&c.scan_req);
+                            ++scan_uses;
                         }
-                    }
-                    if (!ok) record_timeout(hdr, epoch, t);
-                    // block exclusive scan of the thread sums `run`
-                    Acc inc = run;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const Acc o = shfl_up_acc<Op>(inc, d);
-                        if (lane >= d) inc = Op::combine(o, inc);
-                    }
-                    if (lane == 31) c.wtot_v[warp] = inc;
-                    named_barrier_sync<CTHREADS>(1);
-                    Acc ex = shfl_up_acc<Op>(inc, 1);
-                    if (lane == 0) ex = Op::identity();
-                    Acc wpre = Op::identity();
-                    for (int w = 0; w < warp; ++w) wpre = Op::combine(wpre, c.wtot_v[w]);
-                    ex = Op::combine(wpre, ex);
-                    Acc chunk_total = Op::identity();
-                    for (int w = 0; w < CWARPS; ++w) chunk_total = Op::combine(chunk_total, c.wtot_v[w]);
-#pragma unroll
-                    for (int q = 0; q < kChunkPerThread; ++q) {
-                        const int64_t i = i0 + q;
-                        if (q < per && i < first + nch) {
-                            // the in-chunk offset replaces the sum (state P)
-                            publish<Op>(p.rec, i, epoch, kStateP, false, ex);
-                            ex = Op::combine(ex, sv[q]);
-                        }
-                    }
-                    named_barrier_sync<CTHREADS>(1);
-                    if (tid == 0) {
-                        Acc e = Op::identity();
-                        if (ch > 0) {
-                            uint32_t st = kStateX;
-                            bool hf;
-                            const uint64_t t0 = global_timer_ns();
-                            while (true) {
-                                read_words<Op>(rec_chunk(p.rec, ch - 1, 2), rec_chunk(p.rec, ch - 1, 3),
-                                               epoch, st, hf, e);
-                                if (st == kStateP) break;
-                                if (global_timer_ns() - t0 > cfg.spin_limit_ns ||
-                                    launch_aborted(hdr, epoch)) {
-                                    record_timeout(hdr, epoch, t);
-                                    e = Op::identity();
-                                    break;
-                                }
-                                __nanosleep(64);
-                                poll_round_fence();
-                            }
-                        }
-                        publish_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch,
-                                          kStateP, false, e);
-                        publish_words<Op>(rec_chunk(p.rec, ch, 2), rec_chunk(p.rec, ch, 3), epoch,
-                                          kStateP, false, Op::combine(e, chunk_total));
                     }
                 }
                 continue;
@@ -350,7 +453,7 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) partitioned_kernel(co
             if (tid == 0) {
                 // the prefetched copies first; poll the status words themselves
                 // only if a copy was taken before its word was published
-                const int64_t ch = t / K;
+                const int64_t ch = static_cast<uint32_t>(t) / static_cast<uint32_t>(K);
                 Acc e, off;
                 uint32_t se, so;
                 bool hf;
@@ -401,6 +504,22 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) partitioned_kernel(co
         if (tid == 0 && pending >= 0) {
             bulk_wait_read_all();
             mbar_arrive(&c.empty[pending]);
+        }
+        if (tid == 0) {
+            // stop the scanner warp once its last request is done
+            if (scan_uses > 0 && scan_ok)
+                scan_ok = mbar_wait_bounded(&c.scan_idle, (scan_uses - 1) & 1u, role_limit, hdr, epoch, true);
+            c.scan_chunk = -1;
+            mbar_arrive(&c.scan_req);
+        }
+    } else if (warp == SCAN_WARP) {
+        for (uint32_t u = 0;; ++u) {
+            if (!warp_wait(&c.scan_req, u & 1u, role_limit, hdr, epoch, lane)) break;
+            const int64_t ch = *static_cast<volatile int64_t*>(&c.scan_chunk);
+            if (ch < 0) break;
+            chunk_scan_warp<Op>(p, ch, hdr, epoch, cfg, lane);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&c.scan_idle);
         }
     }
 

@@ -230,23 +230,26 @@ print("ok")
 """
 
 
-def test_partitioned_many_small_chunks(tmp_path):
+@pytest.mark.parametrize("lag", [1, 2, 5])
+def test_partitioned_many_small_chunks(tmp_path, lag):
     """The partitioned scan with the smallest chunks (16 tiles, set through
-    GBSCAN_CHUNK_BYTES in a child process): dozens of chunk prefixes chained."""
+    GBSCAN_CHUNK_BYTES in a child process): dozens of chunk prefixes chained,
+    with the second pass of a chunk 1, 2 or 5 chunks behind its first pass
+    (GBSCAN_CHUNK_LAG)."""
     import os
     import subprocess
     import sys
     from conftest import ROOT
     script = tmp_path / "part.py"
     script.write_text(PARTITION_SCRIPT)
-    env = dict(os.environ, GBSCAN_CHUNK_BYTES="4096")
+    env = dict(os.environ, GBSCAN_CHUNK_BYTES="4096", GBSCAN_CHUNK_LAG=str(lag))
     r = subprocess.run([sys.executable, str(script), ROOT], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
 
 
 def test_partitioned_multi_chunk_default_size():
-    """Default 32 MiB chunks: an array of several chunks plus a ragged tail."""
+    """Default 24 MiB chunks: an array of several chunks plus a ragged tail."""
     n = 7 * 1228 * 5120 + 12345
     a = synth.uniform_i32(n, 256, seed=11)
     x = to_dev(a)
