@@ -54,7 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--algo", choices=["auto", "single_pass", "two_pass", "partitioned"],
-                    default="single_pass", help="scan algorithm of the timed step")
+                    default="auto", help="scan algorithm of the timed step (auto: the tuned "
+                    "fastest algorithm and variant for this GPU and size)")
     ap.add_argument("--n-log2", type=int, default=N_LOG2,
                     help="array size 2^k (profiling runs use a smaller case; the benchmark "
                          "workload is 2^30)")
@@ -279,39 +280,44 @@ def side_measurements(dev, peak) -> dict:
     x.random_(0, VALUE_RANGE)
     y = torch.empty_like(x)
     ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_SCAN, N), dev)
+    from paper_2312_14874_gb300 import autotune
+
+    def pick(fam, n, algo):
+        return autotune.choose(fam, fam[5:], n, algo)[1]
+
     rec("i32_2^30_exclusive", 8 * N, cuda_time_ms(lambda: gb.exclusive(x, out=y, workspace=ws), reps)[0])
-    rec("i32_2^30_two_pass", 8 * N, cuda_time_ms(
-        lambda: gb.inclusive(x, out=y, workspace=ws, algo="two_pass"), reps)[0])
-    rec("i32_2^30_partitioned", 8 * N, cuda_time_ms(
-        lambda: gb.inclusive(x, out=y, workspace=ws, algo="partitioned"), reps)[0])
+    for algo in ("single_pass", "two_pass", "partitioned"):
+        v = pick("scan_i32", N, algo)
+        rec(f"i32_2^30_{algo}", 8 * N, cuda_time_ms(
+            lambda: gb.inclusive(x, out=y, workspace=ws, algo=algo, variant=v), reps)[0])
     rec("copy_torch_4GiB", 8 * N, cuda_time_ms(lambda: y.copy_(x), reps)[0])
     rec("copy_gbscan_4GiB", 8 * N, cuda_time_ms(lambda: gb.copy_(y, x), reps)[0])
-    for v in range(gb.num_variants(torch.int32)):
-        rec(f"i32_2^30_variant{v}", 8 * N, cuda_time_ms(
-            lambda: gb.inclusive(x, out=y, workspace=ws, variant=v), reps)[0])
+    for algo in ("single_pass", "partitioned"):
+        for v in range(gb.num_variants(torch.int32)):
+            rec(f"i32_2^30_{algo}_variant{v}", 8 * N, cuda_time_ms(
+                lambda: gb.inclusive(x, out=y, workspace=ws, algo=algo, variant=v), reps)[0])
     del x, y
     # int64 2^29
     n64 = 1 << 29
     x = torch.empty(n64, dtype=torch.int64, device=dev).random_(0, 1 << 32)
     y = torch.empty_like(x)
-    rec("i64_2^29_single_pass", 16 * n64, cuda_time_ms(lambda: gb.inclusive(x, out=y, workspace=ws), reps)[0])
-    rec("i64_2^29_two_pass", 16 * n64, cuda_time_ms(
-        lambda: gb.inclusive(x, out=y, workspace=ws, algo="two_pass"), reps)[0])
-    rec("i64_2^29_partitioned", 16 * n64, cuda_time_ms(
-        lambda: gb.inclusive(x, out=y, workspace=ws, algo="partitioned"), reps)[0])
+    for algo in ("single_pass", "two_pass", "partitioned"):
+        v = pick("scan_i64", n64, algo)
+        rec(f"i64_2^29_{algo}", 16 * n64, cuda_time_ms(
+            lambda: gb.inclusive(x, out=y, workspace=ws, algo=algo, variant=v), reps)[0])
     del x, y
     # fp32 2^28, plain and compensated
     nf = 1 << 28
     x = torch.randn(nf, device=dev)
     y = torch.empty_like(x)
-    rec("f32_2^28_plain", 8 * nf, cuda_time_ms(lambda: gb.inclusive(x, out=y, workspace=ws), reps)[0])
-    rec("f32_2^28_compensated", 8 * nf, cuda_time_ms(
-        lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True), reps)[0])
-    rec("f32_2^28_partitioned", 8 * nf, cuda_time_ms(
-        lambda: gb.inclusive(x, out=y, workspace=ws, algo="partitioned"), reps)[0])
-    rec("f32_2^28_compensated_partitioned", 8 * nf, cuda_time_ms(
-        lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True, algo="partitioned"),
-        reps)[0])
+    for algo in ("single_pass", "partitioned"):
+        v = pick("scan_f32", nf, algo)
+        rec(f"f32_2^28_plain_{algo}", 8 * nf, cuda_time_ms(
+            lambda: gb.inclusive(x, out=y, workspace=ws, algo=algo, variant=v), reps)[0])
+        v = pick("scan_f32c", nf, algo)
+        rec(f"f32_2^28_compensated_{algo}", 8 * nf, cuda_time_ms(
+            lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True, algo=algo, variant=v),
+            reps)[0])
     del x, y
     # segmented: 65,536 log-uniform segments in [1, 2^16], exclusive, CUDA graph
     off = synth.segment_offsets(65536, max_log2=16, seed=0)
@@ -375,11 +381,14 @@ def main(argv=None) -> int:
     x = h_in.to(dev)
     y = torch.empty_like(x)
     ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_SCAN, N), dev)
-    variant = autotune.choose("scan_i32", "i32", N)
+    algo, variant = autotune.choose("scan_i32", "i32", N, args.algo)
+    if algo == "auto":  # no tuned table: the library's own rule, spelled out
+        algo = "partitioned" if 4 * N >= (128 << 20) else "two_pass"
+    launches_per_step = 3 if algo == "two_pass" else 1
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        gb.inclusive(x, out=y, workspace=ws, variant=variant, algo=args.algo)
+        gb.inclusive(x, out=y, workspace=ws, variant=variant, algo=algo)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -421,7 +430,7 @@ def main(argv=None) -> int:
 
         def e2e_step():
             x.copy_(h_in, non_blocking=True)
-            gb.inclusive(x, out=y, workspace=ws, variant=variant, algo=args.algo)
+            gb.inclusive(x, out=y, workspace=ws, variant=variant, algo=algo)
             h_out.copy_(y, non_blocking=True)
 
         e2e_step()
@@ -455,20 +464,27 @@ def main(argv=None) -> int:
     try:
         with open(prof) as f:
             tj = json.load(f)
-        if tj.get("kernel_variant") == variant and tj.get("source_stamp") == _source_stamp():
+        if (tj.get("kernel_variant") == variant and tj.get("algo") == algo
+                and tj.get("source_stamp") == _source_stamp()):
             traffic = tj.get("bytes_per_launch_full")
     except (OSError, ValueError):
         pass
 
     if rank == 0:
         vinfo = gb.variant_info(torch.int32, _capi.KIND_SCAN, variant)
+        if algo == "partitioned":
+            # the partitioned kernel of a variant: its consumer warps, a loader
+            # warp and a chunk scanner warp; at least three stages
+            cw = vinfo["tile"] // (32 * vinfo["items"])
+            vinfo = {"threads": (cw + 2) * 32, "items": vinfo["items"],
+                     "stages": max(vinfo["stages"], 3), "tile": vinfo["tile"]}
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "dtype": "int32", "values": "uniform [0,255]",
-                       "algo": args.algo, "variant": variant, **vinfo,
+                       "algo": algo, "variant": variant, **vinfo,
                        "l2": "inputs and outputs 4 GiB each, larger than the 129 MB L2: no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -477,7 +493,7 @@ def main(argv=None) -> int:
                          "bytes_per_launch": BYTES_PER_STEP,
                          "avg_launch_ms": round(avg_launch_ms, 4)},
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "device_status": dev_status,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"],

@@ -60,7 +60,7 @@ typedef enum {
 } gbscan_status;
 
 typedef enum {
-    GBSCAN_ALGO_AUTO = 0,        /* the single-pass scan */
+    GBSCAN_ALGO_AUTO = 0,        /* PARTITIONED from 128 MiB of input, else TWO_PASS */
     GBSCAN_ALGO_SINGLE_PASS = 1, /* chained scan with decoupled look-back */
     GBSCAN_ALGO_TWO_PASS = 2,    /* reduce tiles, scan the tile sums, scan with offsets */
     GBSCAN_ALGO_PARTITIONED = 3  /* cache-friendly partitioned two-pass (Section 2.2):
@@ -96,13 +96,15 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
  *   in, out   : device arrays of n elements (out == in allowed).
  *   n         : element count, >= 0.
  *   ws        : zeroed workspace of ws_bytes >= gbscan_workspace_size(dtype, SCAN, n, 0).
- *   algo      : GBSCAN_ALGO_AUTO / SINGLE_PASS (one launch), TWO_PASS (three launches:
- *               tile reduce, one-block scan of the tile sums, scan with offsets), or
- *               PARTITIONED (one launch: the array is cut into chunks of about 24 MiB
- *               (environment variable GBSCAN_CHUNK_BYTES overrides); each chunk is
- *               reduced tile by tile, its tile sums are scanned, and it is scanned a
- *               second time while still in L2, overlapped with the reduction of the
- *               chunk two ahead).
+ *   algo      : GBSCAN_ALGO_SINGLE_PASS (one launch), TWO_PASS (three launches:
+ *               tile reduce, one-block scan of the tile sums, scan with offsets),
+ *               PARTITIONED (one launch: the array is cut into chunks of about 12 MiB,
+ *               environment variable GBSCAN_CHUNK_BYTES; each chunk is reduced tile by
+ *               tile, its tile sums are scanned, and it is scanned a second time while
+ *               still in L2, overlapped with the reduction of the chunk three ahead,
+ *               GBSCAN_CHUNK_LAG), or AUTO (PARTITIONED for inputs of 128 MiB or
+ *               more, TWO_PASS below and for compensated fp32 at any size: the
+ *               fastest choice measured on GB300).
  *   variant   : launch shape (threads, items per thread, pipeline stages), 0 = default;
  *               see gbscan_num_variants / gbscan_variant_info.
  *   mode      : (f32 only) plain fp32 or compensated two-sum carries.

@@ -99,7 +99,7 @@ def _variant(kind: str, dtype_key: str, n: int, variant) -> int:
     if variant is not None:
         return int(variant)
     from . import autotune
-    return autotune.choose(kind, dtype_key, n)
+    return autotune.choose(kind, dtype_key, n)[1]
 
 
 def scan(x: torch.Tensor, exclusive: bool = False, *, out: torch.Tensor | None = None,
@@ -123,7 +123,13 @@ def scan(x: torch.Tensor, exclusive: bool = False, *, out: torch.Tensor | None =
     if compensated and x.dtype != torch.float32:
         raise ValueError("compensated mode applies to float32")
     kind_key = "scan_" + key + ("c" if compensated else "")
-    v = _variant(kind_key, key, n, variant)
+    if algo not in _ALGOS:
+        raise ValueError(f"unknown algo {algo!r}")
+    if variant is None:
+        from . import autotune
+        algo, v = autotune.choose(kind_key, key, n, algo)
+    else:
+        v = int(variant)
     ws = workspace or _workspace_for(x.device, workspace_bytes(x.dtype, _capi.KIND_SCAN, n))
     s = _stream_handle(x.device)
     L = _capi.lib()

@@ -49,26 +49,46 @@ def _table(key: str) -> dict:
         return _tables[key]
 
 
-def choose(kind_key: str, dtype_key: str, n: int) -> int:
-    """Variant for a kernel family at size n: the tuned winner of the nearest
-    size bucket at or above log2(n), else the largest bucket, else 0."""
-    forced = os.environ.get("GBSCAN_VARIANT")
-    if forced is not None:
-        return int(forced)
+ALGOS = ("single_pass", "two_pass", "partitioned")
+
+
+def _entry(kind_key: str, n: int):
+    """The tuned entry of the nearest size bucket at or above log2(n), else of
+    the largest bucket, else None."""
     try:
         t = _table(gpu_key())
     except Exception:
-        return 0
+        return None
     entries = t.get(kind_key)
     if not entries:
-        return 0
+        return None
     b = max(0, math.ceil(math.log2(max(n, 1))))
     best = None
-    for bucket, variant in sorted((int(k), int(v)) for k, v in entries.items()):
-        best = variant
+    for bucket, entry in sorted(((int(k), v) for k, v in entries.items()), key=lambda kv: kv[0]):
+        best = entry
         if bucket >= b:
-            return variant
-    return best if best is not None else 0
+            return entry
+    return best
+
+
+def choose(kind_key: str, dtype_key: str, n: int, algo: str = "auto") -> tuple[str, int]:
+    """(algorithm, variant) for a kernel family at size n.  For plain scans a
+    tuned entry holds the fastest variant of every algorithm and the fastest
+    pair overall ("best"), which is what algo="auto" takes; other families
+    have one algorithm and an entry is the variant.  Without a table: the
+    requested algorithm (the library's own AUTO rule for "auto") and variant 0."""
+    forced = os.environ.get("GBSCAN_VARIANT")
+    if forced is not None:
+        return algo, int(forced)
+    entry = _entry(kind_key, n)
+    if entry is None:
+        return algo, 0
+    if isinstance(entry, dict):
+        if algo == "auto":
+            a, v = entry["best"].split(":")
+            return a, int(v)
+        return algo, int(entry.get(algo, 0))
+    return algo, int(entry)
 
 
 def _time_ms(fn, reps: int = 10, warmup: int = 3) -> float:
@@ -88,41 +108,69 @@ def _time_ms(fn, reps: int = 10, warmup: int = 3) -> float:
     return times[len(times) // 2]
 
 
-def tune(sizes_log2=(20, 24, 28, 30), write: bool = True, families=None,
+def tune(sizes_log2=(20, 22, 24, 26, 28, 30), write: bool = True, families=None,
          verbose: bool = True) -> dict:
     """Time every variant of every family over the size ladder and record the
-    fastest per (family, size bucket).  Inputs are zeros of each size (the
-    kernels' cost does not depend on the values)."""
+    fastest per (family, size bucket); for plain scans, every variant of every
+    algorithm.  Inputs are zeros of each size (the kernels' cost does not
+    depend on the values)."""
     import paper_2312_14874_gb300 as gb
     from . import _capi
 
     dev = torch.device("cuda", torch.cuda.current_device())
     free = torch.cuda.mem_get_info(dev)[0]
-    plan = {
-        "scan_i32": (torch.int32, _capi.KIND_SCAN, lambda x, y, v: gb.scan(x, out=y, variant=v)),
-        "scan_i64": (torch.int64, _capi.KIND_SCAN, lambda x, y, v: gb.scan(x, out=y, variant=v)),
-        "scan_f32": (torch.float32, _capi.KIND_SCAN, lambda x, y, v: gb.scan(x, out=y, variant=v)),
-        "scan_f32c": (torch.float32, _capi.KIND_SCAN,
-                      lambda x, y, v: gb.scan(x, out=y, variant=v, compensated=True)),
-        "scan_f64": (torch.float64, _capi.KIND_SCAN, lambda x, y, v: gb.scan(x, out=y, variant=v)),
-        "rows_f32": (torch.float32, _capi.KIND_ROWS,
-                     lambda x, y, v: gb.rows(x.view(-1, 8192), out=y.view(-1, 8192), variant=v)),
-        "bwd_f32": (torch.float32, _capi.KIND_ROWS,
-                    lambda x, y, v: gb.backward(x.view(-1, 8192), out=y.view(-1, 8192), variant=v)),
+    plain = {
+        "scan_i32": (torch.int32, False),
+        "scan_i64": (torch.int64, False),
+        "scan_f32": (torch.float32, False),
+        "scan_f32c": (torch.float32, True),
+        "scan_f64": (torch.float64, False),
+    }
+    rowwise = {
+        "rows_f32": (torch.float32, lambda x, y, v: gb.rows(x.view(-1, 8192), out=y.view(-1, 8192), variant=v)),
+        "bwd_f32": (torch.float32, lambda x, y, v: gb.backward(x.view(-1, 8192), out=y.view(-1, 8192),
+                                                                variant=v)),
     }
     if families:
-        plan = {k: v for k, v in plan.items() if k in families}
+        plain = {k: v for k, v in plain.items() if k in families}
+        rowwise = {k: v for k, v in rowwise.items() if k in families}
     key = gpu_key(dev)
     result: dict = {}
-    for fam, (dtype, kind, call) in plan.items():
-        nv = gb.num_variants(dtype, kind)
-        result[fam] = {}
+
+    def sizes(dtype):
+        esz = torch.empty((), dtype=dtype).element_size()
         for lg in sizes_log2:
-            n = 1 << lg
-            esz = torch.empty((), dtype=dtype).element_size()
-            if 2 * n * esz > 0.6 * free:
+            if 2 * (1 << lg) * esz <= 0.6 * free:
+                yield lg
+
+    for fam, (dtype, comp) in plain.items():
+        result[fam] = {}
+        nv = gb.num_variants(dtype, _capi.KIND_SCAN)
+        for lg in sizes(dtype):
+            x = torch.zeros(1 << lg, dtype=dtype, device=dev)
+            y = torch.empty_like(x)
+            entry, best_t = {}, None
+            for algo in ALGOS:
+                times = [_time_ms(lambda: gb.scan(x, out=y, algo=algo, variant=v, compensated=comp))
+                         for v in range(nv)]
+                v = min(range(nv), key=lambda i: times[i])
+                entry[algo] = v
+                if best_t is None or times[v] < best_t:
+                    best_t, entry["best"] = times[v], f"{algo}:{v}"
+                if verbose:
+                    print(f"[tune] {fam} n=2^{lg} {algo}: " +
+                          ", ".join(f"v{i}={t * 1e3:.1f}us" for i, t in enumerate(times)), flush=True)
+            result[fam][str(lg)] = entry
+            if verbose:
+                print(f"[tune] {fam} n=2^{lg} -> {entry['best']}", flush=True)
+            del x, y
+    for fam, (dtype, call) in rowwise.items():
+        result[fam] = {}
+        nv = gb.num_variants(dtype, _capi.KIND_ROWS)
+        for lg in sizes(dtype):
+            if lg < 13:
                 continue
-            x = torch.zeros(n, dtype=dtype, device=dev)
+            x = torch.zeros(1 << lg, dtype=dtype, device=dev)
             y = torch.empty_like(x)
             times = [_time_ms(lambda: call(x, y, v)) for v in range(nv)]
             best = min(range(nv), key=lambda v: times[v])

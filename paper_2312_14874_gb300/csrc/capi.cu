@@ -146,6 +146,13 @@ static long long env_cached(std::atomic<long long>& cache, const char* name, lon
     return v;
 }
 
+// GBSCAN_ALGO_AUTO takes the partitioned scan from this input size on and the
+// two-pass scan below it, where the data stays in L2 between the passes anyway
+// (measured on GB300: two-pass is the fastest up to 64 MiB, partitioned from
+// 256 MiB; compensated fp32, whose scan is bound by its TwoSum chains, is
+// fastest two-pass at every size).
+constexpr uint64_t kAutoPartitionedBytes = 128ull << 20;
+
 int64_t partition_chunk_tiles(const Variant& v, size_t esz) {
     static std::atomic<long long> bytes_cache{0};
     const long long bytes = env_cached(bytes_cache, "GBSCAN_CHUNK_BYTES", 12ll << 20);
@@ -183,6 +190,10 @@ gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n,
     Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
     p.exclusive = exclusive;
     cudaGetLastError();  // clear a stale, non-sticky error of an earlier call
+    if (algo == GBSCAN_ALGO_AUTO)
+        algo = (v.partitioned && static_cast<uint64_t>(n) * esz >= kAutoPartitionedBytes)
+                   ? GBSCAN_ALGO_PARTITIONED
+                   : GBSCAN_ALGO_TWO_PASS;
     if (algo == GBSCAN_ALGO_PARTITIONED) {
         if (!v.partitioned) return GBSCAN_ERR_UNSUPPORTED;
         p.chunk_tiles = partition_chunk_tiles(v, esz);
@@ -324,6 +335,7 @@ static gbscan_status scan_f32_impl(const float* in, float* out, int64_t n, gbsca
                                    int variant, cudaStream_t stream) {
     if (mode != GBSCAN_F32_PLAIN && mode != GBSCAN_F32_COMPENSATED) return GBSCAN_ERR_INVALID_ARG;
     const Family& fam = mode == GBSCAN_F32_COMPENSATED ? family_scan_f32c() : family_scan_f32();
+    if (mode == GBSCAN_F32_COMPENSATED && algo == GBSCAN_ALGO_AUTO) algo = GBSCAN_ALGO_TWO_PASS;
     return scan_flat(fam, in, out, n, sizeof(float), excl, ws, ws_bytes, algo, variant, stream);
 }
 

@@ -135,6 +135,20 @@ constexpr int kClaim = 2;
 // Most tiles a chunk may have.
 constexpr int kMaxChunkTiles = 1 << 16;
 
+// Publishes tile t's sum (state A) for the chunk scan, with the test hooks of
+// the workspace header: the dropped tile never publishes, and a pseudo-random
+// sleep of up to delay_max ns precedes every publication (race stress).
+template <class Op>
+__device__ __forceinline__ void publish_sum_hooked(unsigned long long* rec, int64_t t, uint32_t epoch,
+                                                   const LookbackCfg& cfg, typename Op::Acc sum) {
+    if (t == cfg.drop_tile) return;
+    if (cfg.delay_max) {
+        const uint32_t dly = mix32(static_cast<uint64_t>(t) * 0x9e3779b97f4a7c15ull) % (cfg.delay_max + 1);
+        if (dly) __nanosleep(dly);
+    }
+    publish<Op>(rec, t, epoch, kStateA, false, sum);
+}
+
 // Issues the reads of R status-word rows (32 tiles each, row q of the batch
 // holding tiles r0 + 32q .. r0 + 32q + 31 of the chunk that starts at tile
 // `first`); tiles at or past nch are left as zero words.
@@ -253,6 +267,10 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
                 __nanosleep(64);
                 poll_round_fence();
             }
+        }
+        if (cfg.delay_max) {
+            const uint32_t dly = mix32(static_cast<uint64_t>(ch) * 0x2545f4914f6cdd1dull) % (cfg.delay_max + 1);
+            if (dly) __nanosleep(dly);
         }
         publish_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, kStateP, false, e);
         publish_words<Op>(rec_chunk(p.rec, ch, 2), rec_chunk(p.rec, ch, 3), epoch, kStateP, false,
@@ -425,7 +443,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 if (tid == 0) {
                     Acc total = Op::identity();
                     for (int w = 0; w < CWARPS; ++w) total = Op::combine(total, c.wtot_v[w]);
-                    publish<Op>(p.rec, t, epoch, kStateA, false, total);
+                    publish_sum_hooked<Op>(p.rec, t, epoch, cfg, total);
                     mbar_arrive(&c.empty[s]);  // every thread holds its items: stage free
                 }
                 if (tid == 0) {

@@ -38,7 +38,7 @@ def test_race_stress_random_publication_delays():
     gb.set_debug(delay_ns_max=3000, workspace=ws)
     for rep in range(40):
         v = rep % gb.num_variants(torch.int32)
-        y = gb.inclusive(x, variant=v, workspace=ws).cpu().numpy()
+        y = gb.inclusive(x, variant=v, workspace=ws, algo="single_pass").cpu().numpy()
         assert gb.device_status(ws) == 0, (rep, v)
         assert np.array_equal(y, want), (rep, v)
     gb.set_debug(workspace=ws)
@@ -61,25 +61,79 @@ def test_race_stress_segmented_and_i64():
         assert np.array_equal(gb.segmented(x, o, exclusive=True, workspace=ws, variant=v)
                               .cpu().numpy(), want), rep
         assert gb.device_status(ws) == 0, rep
-        assert np.array_equal(gb.inclusive(xb, workspace=ws, variant=rep % 5).cpu().numpy(),
-                              want64), rep
+        assert np.array_equal(gb.inclusive(xb, workspace=ws, variant=rep % 5, algo="single_pass")
+                              .cpu().numpy(), want64), rep
         assert gb.device_status(ws) == 0, rep
     gb.set_debug(workspace=ws)
     assert gb.device_status(ws) == 0
 
 
+PARTITION_STRESS = r"""
+import sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import oracle, synth
+import paper_2312_14874_gb300 as gb
+from paper_2312_14874_gb300 import _capi
+dev = torch.device("cuda", 0)
+n = 16 * 5120 * 23 + 777
+a = synth.uniform_i32(n, 1 << 16, seed=9)
+want_in, want_ex = oracle.scan_i32(a, False), oracle.scan_i32(a, True)
+b = synth.uniform_i64(n // 2, 1 << 32, seed=10)
+want64 = oracle.scan_i64(b)
+x, xb = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+ws = gb.Workspace(gb.workspace_bytes(torch.int64, _capi.KIND_SCAN, n))
+gb.set_debug(delay_ns_max=3000, workspace=ws)
+for rep in range(24):
+    v = rep % gb.num_variants(torch.int32)
+    excl = rep % 2 == 1
+    y = gb.scan(x, excl, workspace=ws, algo="partitioned", variant=v).cpu().numpy()
+    assert gb.device_status(ws) == 0, (rep, v)
+    assert np.array_equal(y, want_ex if excl else want_in), (rep, v)
+    y = gb.inclusive(xb, workspace=ws, algo="partitioned", variant=v).cpu().numpy()
+    assert gb.device_status(ws) == 0, (rep, v)
+    assert np.array_equal(y, want64), (rep, v)
+gb.set_debug(workspace=ws)
+assert gb.device_status(ws) == 0
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("lag", [1, 3])
+def test_race_stress_partitioned_small_chunks(tmp_path, lag):
+    """Pseudo-random sleeps before every tile-sum and chunk-prefix publication
+    of the partitioned scan, with 16-tile chunks (set in a child process):
+    dozens of chunk scans and chained chunk prefixes reordered in time, results
+    bit-exact on every repetition."""
+    import os
+    import subprocess
+    import sys
+    from conftest import ROOT
+    script = tmp_path / "stress.py"
+    script.write_text(PARTITION_STRESS)
+    env = dict(os.environ, GBSCAN_CHUNK_BYTES="4096", GBSCAN_CHUNK_LAG=str(lag))
+    r = subprocess.run([sys.executable, str(script), ROOT], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("algo", ["single_pass", "partitioned"])
 @pytest.mark.parametrize("dtype", [torch.int32, torch.int64, torch.float32])
-def test_dropped_tile_times_out_and_recovers(dtype):
+def test_dropped_tile_times_out_and_recovers(dtype, algo):
+    """A tile that never publishes (the drop hook) makes the waits on it run out:
+    the single-pass look-back of later tiles, or the partitioned scan's chunk
+    scan and the second pass behind it.  The launch ends with TIMEOUT recorded,
+    and the same workspace works again once the hook is removed."""
     n = 50 * 5120
     ws = gb.Workspace(gb.workspace_bytes(dtype, _capi.KIND_SCAN, n))
     x = torch.ones(n, dtype=dtype, device=dev())
     gb.set_debug(spin_limit_us=2000, drop_tile=17, workspace=ws)
-    gb.inclusive(x, workspace=ws)
+    gb.inclusive(x, workspace=ws, algo=algo)
     assert gb.device_status(ws) == _capi.ERR_TIMEOUT
     assert gb.device_status(ws) == 0  # cleared by the read
     # the workspace is usable again once the hook is removed
     gb.set_debug(workspace=ws)
-    y = gb.inclusive(x, workspace=ws)
+    y = gb.inclusive(x, workspace=ws, algo=algo)
     assert torch.equal(y.long(), torch.arange(1, n + 1, device=dev()))
     assert gb.device_status(ws) == 0
 
@@ -98,7 +152,8 @@ def test_cuda_graph_segmented_replay():
     assert g.device_status() == 0
 
 
-def test_cuda_graph_plain_scan_replay():
+@pytest.mark.parametrize("algo", ["auto", "single_pass", "partitioned"])
+def test_cuda_graph_plain_scan_replay(algo):
     n = (1 << 20) + 5
     x = torch.empty(n, dtype=torch.float32, device=dev())
     y = torch.empty_like(x)
@@ -106,11 +161,11 @@ def test_cuda_graph_plain_scan_replay():
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        gb.inclusive(x.zero_(), out=y, workspace=ws, compensated=True)  # warm-up (lazy init)
+        gb.inclusive(x.zero_(), out=y, workspace=ws, compensated=True, algo=algo)  # lazy init
     torch.cuda.current_stream().wait_stream(s)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        gb.inclusive(x, out=y, workspace=ws, compensated=True)
+        gb.inclusive(x, out=y, workspace=ws, compensated=True, algo=algo)
     for rep in range(10):
         a = synth.normal_f32(n, seed=rep)
         x.copy_(torch.from_numpy(a))
