@@ -41,7 +41,7 @@ N = 1 << N_LOG2
 VALUE_RANGE = 256  # uniform integers in [0, 255]
 BYTES_PER_STEP = 2 * 4 * N  # int32 read + write
 METRIC = "scan GB/s (read+write bytes/device time) and % of HBM roofline; fp32 max rel err"
-WORKLOAD = "int32 inclusive scan, n=2^30, uniform [0,255], seed 0, single-pass decoupled look-back"
+WORKLOAD = "int32 inclusive scan, n=2^30, uniform [0,255], seed 0"
 
 
 def parse_args(argv=None):

@@ -14,21 +14,24 @@
 //   block scan   : warp totals through shared memory, scanned by warp 0; the last
 //                  value is the tile total, broadcast like the carry vector of
 //                  Section 3.1.
-//   look-back    : the tile publishes its total, then warp 0 reads the status of
-//                  up to 32 predecessors at a time and adds their totals until it
-//                  meets a published inclusive prefix; the tile then publishes its
-//                  own inclusive prefix.  This is the "synchronise only with
-//                  adjacent threads" alternative to the counting barrier that
-//                  Section 2.2.1 mentions (StreamScan), with the decoupled
-//                  aggregate/prefix states of Merrill and Garland's single-pass
-//                  scan, and it plays the role of the paper's sums array
-//                  (Section 2.1, Figure 1).
+//   look-back    : the tile publishes its total, then the stage's look-back
+//                  agent warp reads the status of 32 x LB predecessors per round
+//                  and folds their totals until it meets a published inclusive
+//                  prefix (two levels: 16-tile groups publish group states too);
+//                  the tile then publishes its own inclusive prefix.  This is
+//                  the "synchronise only with adjacent threads" alternative to
+//                  the counting barrier that Section 2.2.1 mentions
+//                  (StreamScan), with the decoupled aggregate/prefix states of
+//                  Merrill and Garland's single-pass scan, and it plays the role
+//                  of the paper's sums array (Section 2.1, Figure 1).
 //   store        : results are written back over the tile in shared memory and
 //                  leave with one TMA bulk store.
 //
-// The same kernel, with a mode parameter, gives the two-pass comparison of the
-// paper's "Accumulate + Prefix Sum" (Figure 1b): a reduce-only pass and a
-// scan-with-offset pass around a one-block scan of the tile sums.
+// The same tile code, with a mode parameter, gives the two-pass comparison of
+// the paper's "Accumulate + Prefix Sum" (Figure 1b): a reduce-only pass and a
+// scan-with-offset pass around a one-block scan of the tile sums; and
+// partitioned.cuh builds the cache-friendly partitioned scan (Section 2.2) from
+// the same pieces.
 //
 // Every wait is bounded (a %globaltimer deadline); a wait that runs out records
 // GBSCAN_ERR_TIMEOUT in the workspace and the kernel still finishes.
