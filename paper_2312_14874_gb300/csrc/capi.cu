@@ -228,6 +228,7 @@ gbscan_status scan_rows_impl(const Family& fam, const void* in, void* out, int64
     p.exclusive = exclusive;
     p.cols = cols;
     cudaGetLastError();
+    if (v.rowblock && cols <= v.rowblock_tile) return from_cuda(v.rowblock(p, stream));
     return from_cuda(v.single_pass(p, stream));
 }
 

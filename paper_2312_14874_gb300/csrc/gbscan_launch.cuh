@@ -6,6 +6,7 @@
 
 #include "kernels.cuh"
 #include "partitioned.cuh"
+#include "rows.cuh"
 
 namespace gbscan {
 
@@ -21,6 +22,8 @@ struct Variant {
     LaunchFn scan_offset;  // two-pass: scan with the scanned tile sums
     LaunchFn partitioned;  // cache-friendly partitioned scan (null where not built)
     int max_chunk_tiles;   // partitioned: most tiles a chunk may have
+    LaunchFn rowblock;     // row kinds: whole rows per tile, no look-back (null elsewhere)
+    int rowblock_tile;     // row kinds: the longest row the row-block kernel takes
 };
 
 struct Family {
@@ -95,6 +98,14 @@ cudaError_t launch_pt(const Params& p, cudaStream_t stream) {
                              occ_cache, p, stream);
 }
 
+template <class Op, int CWARPS, int ITEMS, int STAGES, bool REVERSE, int MINB>
+cudaError_t launch_rb(const Params& p, cudaStream_t stream) {
+    static std::atomic<int> occ_cache[64];
+    return launch_persistent(rowblock_kernel<Op, CWARPS, ITEMS, STAGES, REVERSE, MINB>,
+                             rb_threads<CWARPS>(), rb_smem_bytes<Op, CWARPS, ITEMS, STAGES>(),
+                             occ_cache, p, stream);
+}
+
 template <class Op>
 cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStream_t stream) {
     scan_tile_sums_kernel<Op, 1024><<<1, 1024, 0, stream>>>(rec, num_tiles);
@@ -111,6 +122,14 @@ cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStr
     Variant {                                                                                  \
         (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, HEADS_, REV_, LB, MB>, nullptr, \
             nullptr, nullptr, 0                                                                \
+    }
+// Row kinds: the chained kernel with row heads (any row length) and the
+// row-block kernel (RCW consumer warps x RI items, RS stages, RMB blocks per
+// SM) for rows of at most RCW * 32 * RI elements.
+#define GBSCAN_VARIANT_ROWS(OP, CW, I, S, LB, MB, REV_, RCW, RI, RS, RMB)                      \
+    Variant {                                                                                  \
+        (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, kRowHeads, REV_, LB, MB>, \
+            nullptr, nullptr, nullptr, 0, &launch_rb<OP, RCW, RI, RS, REV_, RMB>, RCW * 32 * RI   \
     }
 #define GBSCAN_VARIANT_ALL(OP, CW, I, S, LB, MB, TS)                                          \
     Variant {                                                                                 \

@@ -71,8 +71,15 @@ def test_segmented_bad_offsets_reported():
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 @pytest.mark.parametrize("shape", [(1, 1), (3, 1), (1, 5121), (7, 33), (64, 1000), (5, 20000),
-                                   (1000, 3), (40, 8192)])
+                                   (1000, 3), (40, 8192), (37, 1000), (3, 8960), (2, 10753),
+                                   (9, 4480), (2, 4481), (4096, 1024), (513, 4096)])
 def test_rows_and_backward(dtype, shape):
+    """Every variant, inclusive and exclusive, forward and backward.  Rows that
+    fit a variant's row-block tile (fp32 8960 / 10752 / 10240 elements, fp64
+    4480 / 5376 / 5120) take the row-block kernel, several rows to an item when
+    they are short, with a partial last item; longer rows (20000, 10753 fp32,
+    4481+ fp64) take the chained kernel with row heads.  Row lengths that are
+    not 16-byte multiples take the element-wise load path."""
     rows, cols = shape
     g = (synth.normal_f32 if dtype == torch.float32 else synth.normal_f64)(rows * cols, seed=9)
     g = g.reshape(rows, cols)
