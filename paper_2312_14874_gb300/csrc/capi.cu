@@ -50,6 +50,20 @@ __global__ void segment_locate_kernel(const int64_t* offsets, int64_t num_segmen
     if (bad) record_error(hdr, GBSCAN_ERR_INVALID_ARG, -1);
 }
 
+// Head bitmap of a batched segmented scan (zeroed beforehand): bit i is set
+// when element i starts a segment.  Starts outside [0, n) (empty segments at
+// the end, or malformed offsets, which segment_locate_kernel reports) set
+// nothing.
+__global__ void segment_heads_kernel(const int64_t* offsets, int64_t num_segments, int64_t n,
+                                     uint32_t* bitmap) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < num_segments;
+         j += stride) {
+        const int64_t pos = offsets[j];
+        if (pos >= 0 && pos < n) atomicOr(&bitmap[pos >> 5], 1u << (pos & 31));
+    }
+}
+
 __global__ void set_debug_kernel(Header* hdr, uint32_t spin_limit_us, int64_t drop_tile,
                                  uint32_t delay_ns_max) {
     hdr->spin_limit_us = spin_limit_us;
@@ -89,6 +103,19 @@ int64_t records_for(int64_t n, int tile) { return (n + tile - 1) / tile + 1; }
 
 size_t record_bytes(int64_t records) {
     return static_cast<size_t>((records + 15) / 16) * kRecBlockBytes;
+}
+
+// The head bitmap of a segmented scan sits after the largest record region a
+// call on n elements of this size can use, and covers every variant's last
+// tile: bits for n + kSegBitmapPad elements, in whole 16-byte units.
+constexpr int64_t kSegBitmapPad = 16384;
+
+size_t seg_bitmap_offset(int64_t n, size_t esz) {
+    return kHeaderBytes + record_bytes(records_for(n, esz == 8 ? kMinTile8 : kMinTile4));
+}
+
+size_t seg_bitmap_bytes(int64_t n) {
+    return static_cast<size_t>((n + kSegBitmapPad + 127) / 128) * 16;
 }
 
 gbscan_status check_ws(void* ws, size_t ws_bytes, int64_t records) {
@@ -259,10 +286,27 @@ gbscan_status scan_seg_impl(const Family& fam, const void* in, void* out, int64_
     int64_t blocks = (work + 255) / 256;
     const int64_t max_blocks = static_cast<int64_t>(sms > 0 ? sms : 1) * 8;
     if (blocks > max_blocks) blocks = max_blocks;
+    if (v.partitioned) {
+        const size_t boff = seg_bitmap_offset(n, esz), bbytes = seg_bitmap_bytes(n);
+        if (ws_bytes < boff + bbytes) return GBSCAN_ERR_WORKSPACE;
+        uint32_t* bitmap = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws) + boff);
+        if (cudaMemsetAsync(bitmap, 0, bbytes, stream) != cudaSuccess) return GBSCAN_ERR_CUDA;
+        int64_t hb = (num_segments + 255) / 256;
+        if (hb > max_blocks) hb = max_blocks;
+        if (hb < 1) hb = 1;
+        segment_heads_kernel<<<static_cast<unsigned>(hb), 256, 0, stream>>>(offsets, num_segments, n,
+                                                                            bitmap);
+        p.bitmap = bitmap;
+        p.chunk_tiles = partition_chunk_tiles(v, esz);
+        p.chunk_lag = partition_chunk_lag();
+    }
+    // validates the offsets (and gives the single-pass kernel each tile's
+    // first segment)
     segment_locate_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
         offsets, num_segments, n, v.tile, p.num_tiles, p.rec, p.hdr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return GBSCAN_ERR_CUDA;
+    if (v.partitioned) return from_cuda(v.partitioned(p, stream));
     return from_cuda(v.single_pass(p, stream));
 }
 
@@ -309,6 +353,7 @@ gbscan_status gbscan_workspace_size(gbscan_dtype dtype, gbscan_kind kind, int64_
     const int tile = min_tile(dtype);
     if ((n + tile - 1) / tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
     *bytes = kHeaderBytes + record_bytes(records_for(n, tile));
+    if (kind == GBSCAN_KIND_SEGMENTED) *bytes += seg_bitmap_bytes(n);
     return GBSCAN_OK;
 }
 

@@ -126,6 +126,7 @@ struct Params {
     unsigned long long* rec; // tile records (blocks of 16, see above)
     int64_t rec_capacity;    // tiles the workspace holds records for
     const int64_t* offsets; // segmented: CSR offsets (num_segments + 1)
+    const uint32_t* bitmap; // segmented, partitioned: head bitmap (bit i: element i starts a segment)
     int64_t num_segments;
     int64_t cols;           // row kinds: row length
     int64_t chunk_tiles;    // partitioned scan: tiles per chunk

@@ -90,11 +90,11 @@ cudaError_t launch_tp(const Params& p, cudaStream_t stream) {
                              tp_smem_bytes<Op, THREADS, ITEMS, STAGES>(), occ_cache, p, stream);
 }
 
-template <class Op, int CWARPS, int ITEMS, int STAGES, int MINB>
+template <class Op, int CWARPS, int ITEMS, int STAGES, int MINB, int HEADS>
 cudaError_t launch_pt(const Params& p, cudaStream_t stream) {
     static std::atomic<int> occ_cache[64];
-    return launch_persistent(partitioned_kernel<Op, CWARPS, ITEMS, STAGES, MINB>,
-                             pt_threads<CWARPS>(), pt_smem_bytes<Op, CWARPS, ITEMS, STAGES>(),
+    return launch_persistent(partitioned_kernel<Op, CWARPS, ITEMS, STAGES, MINB, HEADS>,
+                             pt_threads<CWARPS>(), pt_smem_bytes<Op, CWARPS, ITEMS, STAGES, HEADS>(),
                              occ_cache, p, stream);
 }
 
@@ -123,6 +123,15 @@ cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStr
         (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, HEADS_, REV_, LB, MB>, nullptr, \
             nullptr, nullptr, 0                                                                \
     }
+// Batched segmented scans with the partitioned kernel (a head bitmap in place
+// of the offsets lookups): CW consumer warps x I items, S stages, MB blocks per
+// SM; threads counts the consumer, loader and chunk scanner warps.
+#define GBSCAN_VARIANT_SEG_PT(OP, CW, I, S, MB)                                                 \
+    Variant {                                                                                  \
+        (CW + 2) * 32, I, S, CW * 32 * I, nullptr, nullptr, nullptr,                           \
+            &launch_pt<OP, CW, I, S, MB, kOffsetHeads>, kMaxChunkTiles                         \
+    }
+
 // Row kinds: the chained kernel with row heads (any row length) and the
 // row-block kernel (RCW consumer warps x RI items, RS stages, RMB blocks per
 // SM) for rows of at most RCW * 32 * RI elements.
@@ -135,7 +144,7 @@ cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStr
     Variant {                                                                                 \
         (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, kNoHeads, false, LB, MB>, \
             &launch_tp<OP, CW * 32, I, TS, kReduce>, &launch_tp<OP, CW * 32, I, TS, kScanOffset>, \
-            &launch_pt<OP, CW, I, (S > 2 ? S : 3), (MB > 2 ? 2 : MB)>, kMaxChunkTiles                \
+            &launch_pt<OP, CW, I, (S > 2 ? S : 3), (MB > 2 ? 2 : MB), kNoHeads>, kMaxChunkTiles      \
     }
 
 // Families, one per translation unit group.

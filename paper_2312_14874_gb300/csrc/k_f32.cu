@@ -18,13 +18,15 @@ const Family& family_scan_f32() {
 }
 
 static const Variant kSegF32[] = {
+    GBSCAN_VARIANT_SEG_PT(OpF32, 8, 20, 4, 2),
+    GBSCAN_VARIANT_SEG_PT(OpF32, 8, 20, 3, 2),
     GBSCAN_VARIANT_SP(OpF32, 8, 20, 3, 8, 3, kOffsetHeads, false),
     GBSCAN_VARIANT_SP(OpF32, 8, 20, 4, 8, 2, kOffsetHeads, false),
     GBSCAN_VARIANT_SP(OpF32, 16, 20, 2, 8, 2, kOffsetHeads, false),
 };
 
 const Family& family_seg_f32() {
-    static const Family f{3, kSegF32, nullptr};
+    static const Family f{5, kSegF32, nullptr};
     return f;
 }
 

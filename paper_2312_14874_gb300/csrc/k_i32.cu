@@ -18,13 +18,15 @@ const Family& family_scan_i32() {
 }
 
 static const Variant kSegI32[] = {
+    GBSCAN_VARIANT_SEG_PT(OpI32, 8, 20, 4, 2),
+    GBSCAN_VARIANT_SEG_PT(OpI32, 8, 20, 3, 2),
     GBSCAN_VARIANT_SP(OpI32, 8, 20, 3, 8, 3, kOffsetHeads, false),
     GBSCAN_VARIANT_SP(OpI32, 8, 20, 4, 8, 2, kOffsetHeads, false),
     GBSCAN_VARIANT_SP(OpI32, 16, 20, 2, 8, 2, kOffsetHeads, false),
 };
 
 const Family& family_seg_i32() {
-    static const Family f{3, kSegI32, nullptr};
+    static const Family f{5, kSegI32, nullptr};
     return f;
 }
 

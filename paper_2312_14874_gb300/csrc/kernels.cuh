@@ -318,10 +318,11 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
 
             bool tf;
             Acc tv;
-            thread_reduce<Op, ITEMS, HEADS>(x, hm, tf, tv);
+            const bool wh = HEADS != kNoHeads && __any_sync(0xffffffffu, hm != 0u);
+            thread_reduce_w<Op, ITEMS, HEADS>(x, hm, wh, tf, tv);
             bool wf = tf;
             Acc wv = tv;
-            warp_inclusive_scan<Op, HEADS>(wf, wv, lane);
+            warp_inclusive_scan_w<Op, HEADS>(wh, wf, wv, lane);
             bool ef = __shfl_up_sync(0xffffffffu, wf ? 1 : 0, 1) != 0;
             Acc ev = shfl_up_acc<Op>(wv, 1);
             if (lane == 0) {
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
             else
                 ev = Op::combine(gv, ev);
             T y[ITEMS];
-            thread_outputs<Op, ITEMS, HEADS>(x, hm, ev, excl, y);
+            thread_outputs_w<Op, ITEMS, HEADS>(x, hm, wh, ev, excl, y);
             store_items<T, ITEMS, TILE, REVERSE>(buf, tid, y);
             if (tile_fast) fence_proxy_async_smem();
             named_barrier_sync<CTHREADS>(1);

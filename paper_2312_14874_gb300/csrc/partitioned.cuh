@@ -95,7 +95,7 @@ __device__ __forceinline__ void partitioned_item(uint32_t w, const PtOrder& o, u
     tile = static_cast<int64_t>(c) * o.K + w;
 }
 
-template <class Op, int CWARPS, int STAGES, int TILE>
+template <class Op, int CWARPS, int STAGES, int TILE, int HEADS>
 struct PtCtrl {
     using Acc = typename Op::Acc;
     uint64_t full[STAGES];
@@ -106,8 +106,13 @@ struct PtCtrl {
     // 16-byte pair holding lo[t], and the one holding hi[t]) and of the chunk's
     // E words, brought in by the loader's bulk copies
     alignas(16) unsigned long long stat[STAGES][6];
+    // segmented scans: per stage, the tile's slice of the head bitmap (bit i =
+    // element i starts a segment), then zero words for the reads past its end
+    alignas(16) uint32_t bits[HEADS != kNoHeads ? STAGES : 1][HEADS != kNoHeads ? TILE / 32 + 4 : 4];
     Acc wtot_v[CWARPS];
+    uint32_t wtot_f[CWARPS];
     Acc prefix_v;
+    uint32_t prefix_f;
     uint64_t scan_req;   // consumers -> scanner warp: a chunk to scan (or -1: stop)
     uint64_t scan_idle;  // scanner warp -> consumers: the request is done
     int64_t scan_chunk;
@@ -117,10 +122,10 @@ struct PtCtrl {
     unsigned int claim_sink;
 };
 
-template <class Op, int CWARPS, int ITEMS, int STAGES>
+template <class Op, int CWARPS, int ITEMS, int STAGES, int HEADS>
 constexpr int pt_smem_bytes() {
     return STAGES * CWARPS * 32 * ITEMS * static_cast<int>(sizeof(typename Op::T)) +
-           static_cast<int>(sizeof(PtCtrl<Op, CWARPS, STAGES, CWARPS * 32 * ITEMS>));
+           static_cast<int>(sizeof(PtCtrl<Op, CWARPS, STAGES, CWARPS * 32 * ITEMS, HEADS>));
 }
 
 // Consumer warps, the loader warp and the chunk scanner warp.
@@ -135,18 +140,20 @@ constexpr int kClaim = 2;
 // Most tiles a chunk may have.
 constexpr int kMaxChunkTiles = 1 << 16;
 
-// Publishes tile t's sum (state A) for the chunk scan, with the test hooks of
+// Publishes tile t's sum (state A; with segments, the head flag and the sum
+// after the tile's last head) for the chunk scan, with the test hooks of
 // the workspace header: the dropped tile never publishes, and a pseudo-random
 // sleep of up to delay_max ns precedes every publication (race stress).
 template <class Op>
 __device__ __forceinline__ void publish_sum_hooked(unsigned long long* rec, int64_t t, uint32_t epoch,
-                                                   const LookbackCfg& cfg, typename Op::Acc sum) {
+                                                   const LookbackCfg& cfg, bool head,
+                                                   typename Op::Acc sum) {
     if (t == cfg.drop_tile) return;
     if (cfg.delay_max) {
         const uint32_t dly = mix32(static_cast<uint64_t>(t) * 0x9e3779b97f4a7c15ull) % (cfg.delay_max + 1);
         if (dly) __nanosleep(dly);
     }
-    publish<Op>(rec, t, epoch, kStateA, false, sum);
+    publish<Op>(rec, t, epoch, kStateA, head, sum);
 }
 
 // Issues the reads of R status-word rows (32 tiles each, row q of the batch
@@ -178,7 +185,9 @@ __device__ __forceinline__ void chunk_rows_issue(const unsigned long long* rec, 
 // rows of 32 consecutive tiles (the next batch's reads go out before the
 // current batch is scanned); the rows of a batch are scanned independently
 // with warp shuffles, and a running carry joins them in the publishing loop.
-template <class Op>
+// Segmented scans carry (head flag, value) pairs through the same steps with
+// the segmented operator: a value after a head does not add what came before.
+template <class Op, int HEADS>
 __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32_t epoch,
                                 const LookbackCfg& cfg, int lane) {
     using Acc = typename Op::Acc;
@@ -187,18 +196,20 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
     const int64_t first = ch * K;
     const int64_t nch = (p.num_tiles - first) < K ? (p.num_tiles - first) : K;
     Acc carry = Op::identity();
+    bool carry_f = false;
     bool ok = true;
     unsigned long long w0[R], w1[R];
     chunk_rows_issue<Op, R>(p.rec, first, nch, 0, lane, w0, w1);
     for (int64_t r0 = 0; r0 < nch; r0 += 32 * R) {
         Acc v[R];
         uint32_t st[R];
+        bool hfl[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            bool hf;
             v[q] = Op::identity();
+            hfl[q] = false;
             st[q] = kStateA;  // entries past the chunk count as published
-            if (r0 + q * 32 + lane < nch) parse_words<Op>(w0[q], w1[q], epoch, st[q], hf, v[q]);
+            if (r0 + q * 32 + lane < nch) parse_words<Op>(w0[q], w1[q], epoch, st[q], hfl[q], v[q]);
         }
         if (r0 + 32 * R < nch) chunk_rows_issue<Op, R>(p.rec, first, nch, r0 + 32 * R, lane, w0, w1);
         const uint64_t t0 = global_timer_ns();
@@ -216,9 +227,8 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 if (st[q] == kStateX) {
-                    bool hf;
                     const int64_t i = first + r0 + q * 32 + lane;
-                    read_words<Op>(rec_lo(p.rec, i), rec_hi(p.rec, i), epoch, st[q], hf, v[q]);
+                    read_words<Op>(rec_lo(p.rec, i), rec_hi(p.rec, i), epoch, st[q], hfl[q], v[q]);
                 }
             }
         }
@@ -227,24 +237,41 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
         // row scans (independent of one another): ex = exclusive within the
         // row, v = the row's total
         Acc ex[R];
+        bool exf[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
+            bool f = hfl[q];
             Acc inc = v[q];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const Acc o = shfl_up_acc<Op>(inc, d);
-                if (lane >= d) inc = Op::combine(o, inc);
-            }
+            warp_inclusive_scan<Op, HEADS>(f, inc, lane);
+            exf[q] = __shfl_up_sync(0xffffffffu, f ? 1 : 0, 1) != 0;
             ex[q] = shfl_up_acc<Op>(inc, 1);
-            if (lane == 0) ex[q] = Op::identity();
+            if (lane == 0) {
+                exf[q] = false;
+                ex[q] = Op::identity();
+            }
             v[q] = shfl_idx_acc<Op>(inc, 31);
+            hfl[q] = __shfl_sync(0xffffffffu, f ? 1 : 0, 31) != 0;
         }
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int64_t i = r0 + q * 32 + lane;
             // the in-chunk offset replaces the sum (state P)
-            if (i < nch) publish<Op>(p.rec, first + i, epoch, kStateP, false, Op::combine(carry, ex[q]));
-            carry = Op::combine(carry, v[q]);
+            bool of = exf[q];
+            Acc ov = ex[q];
+            if constexpr (HEADS != kNoHeads)
+                seg_combine<Op>(carry_f, carry, of, ov);
+            else
+                ov = Op::combine(carry, ov);
+            if (i < nch) publish<Op>(p.rec, first + i, epoch, kStateP, of, ov);
+            if constexpr (HEADS != kNoHeads) {
+                bool f2 = hfl[q];
+                Acc v2 = v[q];
+                seg_combine<Op>(carry_f, carry, f2, v2);
+                carry_f = f2;
+                carry = v2;
+            } else {
+                carry = Op::combine(carry, v[q]);
+            }
         }
     }
     if (lane == 0) {
@@ -253,12 +280,12 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
             return;
         }
         Acc e = Op::identity();
+        bool ef = false;
         if (ch > 0) {
             uint32_t st = kStateX;
-            bool hf;
             const uint64_t t0 = global_timer_ns();
             while (true) {
-                read_words<Op>(rec_chunk(p.rec, ch - 1, 2), rec_chunk(p.rec, ch - 1, 3), epoch, st, hf, e);
+                read_words<Op>(rec_chunk(p.rec, ch - 1, 2), rec_chunk(p.rec, ch - 1, 3), epoch, st, ef, e);
                 if (st == kStateP) break;
                 if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
                     record_timeout(hdr, epoch, first);
@@ -272,13 +299,18 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
             const uint32_t dly = mix32(static_cast<uint64_t>(ch) * 0x2545f4914f6cdd1dull) % (cfg.delay_max + 1);
             if (dly) __nanosleep(dly);
         }
-        publish_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, kStateP, false, e);
-        publish_words<Op>(rec_chunk(p.rec, ch, 2), rec_chunk(p.rec, ch, 3), epoch, kStateP, false,
-                          Op::combine(e, carry));
+        publish_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, kStateP, ef, e);
+        bool pf = carry_f;
+        Acc pv = carry;
+        if constexpr (HEADS != kNoHeads)
+            seg_combine<Op>(ef, e, pf, pv);
+        else
+            pv = Op::combine(e, carry);
+        publish_words<Op>(rec_chunk(p.rec, ch, 2), rec_chunk(p.rec, ch, 3), epoch, kStateP, pf, pv);
     }
 }
 
-template <class Op, int CWARPS, int ITEMS, int STAGES, int MINB>
+template <class Op, int CWARPS, int ITEMS, int STAGES, int MINB, int HEADS>
 __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(const Params p) {
     using T = typename Op::T;
     using Acc = typename Op::Acc;
@@ -288,7 +320,11 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
     constexpr int LOAD_WARP = CWARPS;
     constexpr int SCAN_WARP = CWARPS + 1;
     static_assert(STAGES >= 2, "a stage is released one store later: at least two stages");
-    using CtrlT = PtCtrl<Op, CWARPS, STAGES, TILE>;
+    static_assert(HEADS == kNoHeads || HEADS == kOffsetHeads, "plain or offset segments");
+    static_assert(HEADS == kNoHeads || (TILE / 8) % 16 == 0, "bitmap slices are bulk copies");
+    static_assert(ITEMS <= 32, "head flags are kept in one 32-bit mask");
+    constexpr uint32_t BITS_BYTES = HEADS != kNoHeads ? TILE / 8 : 0;
+    using CtrlT = PtCtrl<Op, CWARPS, STAGES, TILE, HEADS>;
 
     extern __shared__ __align__(128) unsigned char smem[];
     CtrlT& c = *reinterpret_cast<CtrlT*>(smem + STAGES * TILE_BYTES);
@@ -308,6 +344,9 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
         mbar_init(&c.scan_req, 1);
         mbar_init(&c.scan_idle, 1);
         fence_mbar_init();
+        if constexpr (HEADS != kNoHeads)
+            for (int s = 0; s < STAGES; ++s)
+                for (int w = TILE / 32; w < TILE / 32 + 4; ++w) c.bits[s][w] = 0u;
         c.epoch = hdr->epoch;
         c.clear = 0;
     }
@@ -371,7 +410,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 c.tile_id[s] = t;
                 c.phase[s] = phase;
                 const uint32_t stat_bytes = phase == kItemScan ? (Op::kPacked ? 32u : 48u) : 0u;
-                const uint32_t tx = (fast ? TILE_BYTES : 0u) + stat_bytes;
+                const uint32_t tx = (fast ? TILE_BYTES : 0u) + stat_bytes + BITS_BYTES;
                 if (tx == 0) {
                     mbar_arrive(&c.full[s]);
                 } else {
@@ -379,6 +418,8 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     if (fast)
                         bulk_load_hint(buf, in + t * TILE, TILE_BYTES, &c.full[s],
                                        phase == kItemReduce ? keep : drop);
+                    if constexpr (HEADS != kNoHeads)
+                        bulk_load(&c.bits[s][0], p.bitmap + t * (TILE / 32), BITS_BYTES, &c.full[s]);
                     if (stat_bytes) {
                         // the 16-byte pairs holding the tile's status words, and E
                         unsigned long long* pair = rec_lo(p.rec, t & ~int64_t(1));
@@ -429,21 +470,51 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 for (int j = 0; j < ITEMS; ++j)
                     if (!((valid >> j) & 1u)) x[j] = T(0);
             }
+            uint32_t hm = 0;
+            if constexpr (HEADS != kNoHeads) {
+                // this thread's items in the tile's head bitmap
+                const int b = tid * ITEMS;
+                const uint32_t w = __funnelshift_r(c.bits[s][b >> 5], c.bits[s][(b >> 5) + 1], b & 31);
+                hm = (ITEMS == 32 ? w : (w & ((1u << ITEMS) - 1u)));
+                if (cnt < TILE) hm &= valid_items<ITEMS>(cnt, tid);
+            }
             bool tf;
             Acc tv;
-            thread_reduce<Op, ITEMS, kNoHeads>(x, 0u, tf, tv);
+            const bool wh = HEADS != kNoHeads && __any_sync(0xffffffffu, hm != 0u);
+            thread_reduce_w<Op, ITEMS, HEADS>(x, hm, wh, tf, tv);
 
             if (phase == kItemReduce) {
-                // ---- first pass: the tile sum ------------------------------
+                // ---- first pass: the tile sum (with segments: head flag and
+                // the sum after the tile's last head) --------------------------
+                bool wf = tf;
                 Acc wv = tv;
+                if constexpr (HEADS != kNoHeads) {
+                    warp_inclusive_scan_w<Op, HEADS>(wh, wf, wv, lane);  // lane 31: the warp's
+                    if (lane == 31) {
+                        c.wtot_v[warp] = wv;
+                        c.wtot_f[warp] = wf ? 1u : 0u;
+                    }
+                } else {
 #pragma unroll
-                for (int d = 16; d >= 1; d >>= 1) wv = Op::combine(wv, shfl_down_acc<Op>(wv, d));
-                if (lane == 0) c.wtot_v[warp] = wv;
+                    for (int d = 16; d >= 1; d >>= 1) wv = Op::combine(wv, shfl_down_acc<Op>(wv, d));
+                    if (lane == 0) c.wtot_v[warp] = wv;
+                }
                 named_barrier_sync<CTHREADS>(1);
                 if (tid == 0) {
                     Acc total = Op::identity();
-                    for (int w = 0; w < CWARPS; ++w) total = Op::combine(total, c.wtot_v[w]);
-                    publish_sum_hooked<Op>(p.rec, t, epoch, cfg, total);
+                    bool total_f = false;
+                    for (int w = 0; w < CWARPS; ++w) {
+                        if constexpr (HEADS != kNoHeads) {
+                            bool f2 = c.wtot_f[w] != 0;
+                            Acc v2 = c.wtot_v[w];
+                            seg_combine<Op>(total_f, total, f2, v2);
+                            total_f = f2;
+                            total = v2;
+                        } else {
+                            total = Op::combine(total, c.wtot_v[w]);
+                        }
+                    }
+                    publish_sum_hooked<Op>(p.rec, t, epoch, cfg, total_f, total);
                     mbar_arrive(&c.empty[s]);  // every thread holds its items: stage free
                 }
                 if (tid == 0) {
@@ -474,9 +545,9 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 const int64_t ch = static_cast<uint32_t>(t) / static_cast<uint32_t>(K);
                 Acc e, off;
                 uint32_t se, so;
-                bool hf;
-                parse_words<Op>(c.stat[s][4], c.stat[s][5], epoch, se, hf, e);
-                parse_words<Op>(c.stat[s][t & 1], c.stat[s][2 + (t & 1)], epoch, so, hf, off);
+                bool ef, of;
+                parse_words<Op>(c.stat[s][4], c.stat[s][5], epoch, se, ef, e);
+                parse_words<Op>(c.stat[s][t & 1], c.stat[s][2 + (t & 1)], epoch, so, of, off);
                 const uint64_t t0 = global_timer_ns();
                 while (se != kStateP || so != kStateP) {
                     if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
@@ -486,24 +557,52 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     __nanosleep(64);
                     poll_round_fence();
                     if (se != kStateP)
-                        read_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, se, hf, e);
+                        read_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, se, ef, e);
                     if (so != kStateP)
-                        read_words<Op>(rec_lo(p.rec, t), rec_hi(p.rec, t), epoch, so, hf, off);
+                        read_words<Op>(rec_lo(p.rec, t), rec_hi(p.rec, t), epoch, so, of, off);
                 }
-                c.prefix_v = Op::combine(e, off);
+                // the tile's carry: the chunk prefix, then the in-chunk offset
+                if constexpr (HEADS != kNoHeads) {
+                    seg_combine<Op>(ef, e, of, off);
+                    c.prefix_v = off;
+                    c.prefix_f = of ? 1u : 0u;
+                } else {
+                    c.prefix_v = Op::combine(e, off);
+                }
             }
-            bool wf = false;
+            bool wf = tf;
             Acc wv = tv;
-            warp_inclusive_scan<Op, kNoHeads>(wf, wv, lane);
+            warp_inclusive_scan_w<Op, HEADS>(wh, wf, wv, lane);
+            bool xf = __shfl_up_sync(0xffffffffu, wf ? 1 : 0, 1) != 0;
             Acc ev = shfl_up_acc<Op>(wv, 1);
-            if (lane == 0) ev = Op::identity();
-            if (lane == 31) c.wtot_v[warp] = wv;
+            if (lane == 0) {
+                xf = false;
+                ev = Op::identity();
+            }
+            if (lane == 31) {
+                c.wtot_v[warp] = wv;
+                c.wtot_f[warp] = wf ? 1u : 0u;
+            }
             named_barrier_sync<CTHREADS>(1);
+            // everything before this thread's first item: the tile's carry, the
+            // warps before this one, the lanes before this one
             Acc gv = c.prefix_v;
-            for (int w = 0; w < warp; ++w) gv = Op::combine(gv, c.wtot_v[w]);
-            ev = Op::combine(gv, ev);
+            if constexpr (HEADS != kNoHeads) {
+                bool gf = c.prefix_f != 0;
+                for (int w = 0; w < warp; ++w) {
+                    bool f2 = c.wtot_f[w] != 0;
+                    Acc v2 = c.wtot_v[w];
+                    seg_combine<Op>(gf, gv, f2, v2);
+                    gf = f2;
+                    gv = v2;
+                }
+                seg_combine<Op>(gf, gv, xf, ev);
+            } else {
+                for (int w = 0; w < warp; ++w) gv = Op::combine(gv, c.wtot_v[w]);
+                ev = Op::combine(gv, ev);
+            }
             T y[ITEMS];
-            thread_outputs<Op, ITEMS, kNoHeads>(x, 0u, ev, excl, y);
+            thread_outputs_w<Op, ITEMS, HEADS>(x, hm, wh, ev, excl, y);
             store_items<T, ITEMS, TILE, false>(buf, tid, y);
             if (tile_fast) fence_proxy_async_smem();
             named_barrier_sync<CTHREADS>(1);
@@ -535,7 +634,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             if (!warp_wait(&c.scan_req, u & 1u, role_limit, hdr, epoch, lane)) break;
             const int64_t ch = *static_cast<volatile int64_t*>(&c.scan_chunk);
             if (ch < 0) break;
-            chunk_scan_warp<Op>(p, ch, hdr, epoch, cfg, lane);
+            chunk_scan_warp<Op, HEADS>(p, ch, hdr, epoch, cfg, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&c.scan_idle);
         }

@@ -158,10 +158,11 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) rowblock_kernel(const
             const uint32_t hm = row_heads<ITEMS, REVERSE>(tb, cnt, cols, tid) & valid;
             bool tf;
             Acc tv;
-            thread_reduce<Op, ITEMS, kRowHeads>(x, hm, tf, tv);
+            const bool wh = __any_sync(0xffffffffu, hm != 0u);
+            thread_reduce_w<Op, ITEMS, kRowHeads>(x, hm, wh, tf, tv);
             bool wf = tf;
             Acc wv = tv;
-            warp_inclusive_scan<Op, kRowHeads>(wf, wv, lane);
+            warp_inclusive_scan_w<Op, kRowHeads>(wh, wf, wv, lane);
             bool ef = __shfl_up_sync(0xffffffffu, wf ? 1 : 0, 1) != 0;
             Acc ev = shfl_up_acc<Op>(wv, 1);
             if (lane == 0) {
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) rowblock_kernel(const
             }
             seg_combine<Op>(gf, gv, ef, ev);
             T y[ITEMS];
-            thread_outputs<Op, ITEMS, kRowHeads>(x, hm, ev, excl, y);
+            thread_outputs_w<Op, ITEMS, kRowHeads>(x, hm, wh, ev, excl, y);
             store_items<T, ITEMS, TILE, REVERSE>(buf, tid, y);
             const int off = REVERSE ? TILE - cnt : 0;
             if (fast) fence_proxy_async_smem();

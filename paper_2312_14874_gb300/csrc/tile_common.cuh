@@ -196,4 +196,37 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// Warp-uniform dispatch for segmented kinds.  The flagged versions cost
+// several instructions per element more than the plain ones; a warp none of
+// whose items is a segment head (warp_heads false, decided with __any_sync by
+// the whole warp) takes the plain code, which gives the same result because no
+// flag is ever set in it.
+template <class Op, int ITEMS, int HEADS>
+__device__ __forceinline__ void thread_reduce_w(const typename Op::T (&x)[ITEMS], uint32_t hm,
+                                                bool warp_heads, bool& f, typename Op::Acc& v) {
+    if (HEADS != kNoHeads && warp_heads)
+        thread_reduce<Op, ITEMS, HEADS>(x, hm, f, v);
+    else
+        thread_reduce<Op, ITEMS, kNoHeads>(x, 0u, f, v);
+}
+
+template <class Op, int HEADS>
+__device__ __forceinline__ void warp_inclusive_scan_w(bool warp_heads, bool& f, typename Op::Acc& v,
+                                                      int lane) {
+    if (HEADS != kNoHeads && warp_heads)
+        warp_inclusive_scan<Op, HEADS>(f, v, lane);
+    else
+        warp_inclusive_scan<Op, kNoHeads>(f, v, lane);
+}
+
+template <class Op, int ITEMS, int HEADS>
+__device__ __forceinline__ void thread_outputs_w(const typename Op::T (&x)[ITEMS], uint32_t hm,
+                                                 bool warp_heads, typename Op::Acc gv, bool excl,
+                                                 typename Op::T (&y)[ITEMS]) {
+    if (HEADS != kNoHeads && warp_heads)
+        thread_outputs<Op, ITEMS, HEADS>(x, hm, gv, excl, y);
+    else
+        thread_outputs<Op, ITEMS, kNoHeads>(x, 0u, gv, excl, y);
+}
+
 }  // namespace gbscan

@@ -52,6 +52,12 @@ def test_workspace_size():
     # tile (3072 elements) plus one
     records = -(-(1 << 30) // 3072) + 1
     assert out.value == 256 + 512 * (-(-records // 16))
+    # segmented calls add the head bitmap: one bit per element plus 16384
+    # elements of padding, in 16-byte units
+    n = 386099019
+    assert L.gbscan_workspace_size(_capi.I32, _capi.KIND_SEGMENTED, n, 65536, ctypes.byref(out)) == 0
+    records = -(-n // 3072) + 1
+    assert out.value == 256 + 512 * (-(-records // 16)) + 16 * ((n + 16384 + 127) // 128)
     assert L.gbscan_workspace_size(_capi.I32, _capi.KIND_SCAN, -1, 0, ctypes.byref(out)) == \
         _capi.ERR_INVALID_ARG
     assert L.gbscan_workspace_size(9, _capi.KIND_SCAN, 10, 0, ctypes.byref(out)) == \

@@ -49,7 +49,9 @@ def test_race_stress_segmented_and_i64():
     off = synth.segment_offsets(3000, max_log2=12, seed=2)
     n = int(off[-1])
     a = synth.uniform_i32(n, 4, seed=3)
-    ws = gb.Workspace(gb.workspace_bytes(torch.int64, _capi.KIND_SCAN, n))
+    # one workspace for both kinds: the larger of the two sizes
+    ws = gb.Workspace(max(gb.workspace_bytes(torch.int64, _capi.KIND_SCAN, n),
+                          gb.workspace_bytes(torch.int32, _capi.KIND_SEGMENTED, n, off.size - 1)))
     gb.set_debug(delay_ns_max=2000, workspace=ws)
     x, o = to_dev(a), to_dev(off)
     want = oracle.seg_scan_i32(a, off, True)
@@ -57,7 +59,7 @@ def test_race_stress_segmented_and_i64():
     want64 = oracle.scan_i64(b)
     xb = to_dev(b)
     for rep in range(15):
-        v = rep % 3
+        v = rep % gb.num_variants(torch.int32, _capi.KIND_SEGMENTED)
         assert np.array_equal(gb.segmented(x, o, exclusive=True, workspace=ws, variant=v)
                               .cpu().numpy(), want), rep
         assert gb.device_status(ws) == 0, rep

@@ -59,6 +59,68 @@ def test_segmented(case, dtype_key):
     assert gb.device_status() == 0
 
 
+SEG_PARTITION_SCRIPT = r"""
+import sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import oracle, synth
+import paper_2312_14874_gb300 as gb
+from paper_2312_14874_gb300 import _capi
+dev = torch.device("cuda", 0)
+def random_offsets(n_seg, seed, max_len, empty_frac):
+    lens = synth.uniform_i64(n_seg, max_len + 1, seed=seed, stream=1)
+    drop = synth.unit_f32(n_seg, seed=seed, stream=2) < empty_frac
+    lens = np.where(drop, 0, lens)
+    return np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+cases = {
+    "mixed": random_offsets(400, 12, 20000, 0.1),
+    "spanning_chunks": np.array([0, 1, 700000, 700001, 2000000, 2000000, 2100007], np.int64),
+    "length_one": np.arange(200000 + 1, dtype=np.int64),
+    "log_uniform": synth.segment_offsets(3000, max_log2=12, seed=13),
+}
+for name, off in cases.items():
+    n = int(off[-1])
+    o = torch.from_numpy(off).to(dev)
+    for key in ("i32", "f32"):
+        dt = torch.int32 if key == "i32" else torch.float32
+        a = synth.uniform_i32(n, 4, seed=7) if key == "i32" else synth.unit_f32(n, seed=7)
+        x = torch.from_numpy(a).to(dev)
+        for v in range(gb.num_variants(dt, _capi.KIND_SEGMENTED)):
+            if gb.variant_info(dt, _capi.KIND_SEGMENTED, v)["threads"] != \
+                    (gb.variant_info(dt, _capi.KIND_SEGMENTED, v)["tile"] //
+                     gb.variant_info(dt, _capi.KIND_SEGMENTED, v)["items"] + 64):
+                continue  # the single-pass variants: no chunks
+            for excl in (False, True):
+                y = gb.segmented(x, o, exclusive=excl, variant=v).cpu().numpy()
+                if key == "i32":
+                    assert np.array_equal(y, oracle.seg_scan_i32(a, off, excl)), (name, v, excl)
+                else:
+                    err, k = oracle.max_rel_err(y, oracle.seg_scan_f32_ref(a, off, excl),
+                                                oracle.seg_abs_scan_f32(a, off, excl))
+                    assert err <= 1e-5, (name, v, excl, err, k)
+assert gb.device_status() == 0
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("lag", [1, 3])
+def test_segmented_partitioned_small_chunks(tmp_path, lag):
+    """The segmented scan's partitioned variants with 16-tile chunks (set in a
+    child process): segments spanning many chunks, a head on every element,
+    empty segments; the head flags travel through the tile sums, the chunk
+    scan's offsets and the chained chunk prefixes."""
+    import os
+    import subprocess
+    import sys
+    from conftest import ROOT
+    script = tmp_path / "segpart.py"
+    script.write_text(SEG_PARTITION_SCRIPT)
+    env = dict(os.environ, GBSCAN_CHUNK_BYTES="4096", GBSCAN_CHUNK_LAG=str(lag))
+    r = subprocess.run([sys.executable, str(script), ROOT], env=env, capture_output=True,
+                       text=True, timeout=900)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
 def test_segmented_bad_offsets_reported():
     n = 10000
     x = torch.zeros(n, dtype=torch.int32, device=dev())
