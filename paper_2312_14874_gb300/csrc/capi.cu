@@ -50,18 +50,53 @@ __global__ void segment_locate_kernel(const int64_t* offsets, int64_t num_segmen
     if (bad) record_error(hdr, GBSCAN_ERR_INVALID_ARG, -1);
 }
 
-// Head bitmap of a batched segmented scan (zeroed beforehand): bit i is set
-// when element i starts a segment.  Starts outside [0, n) (empty segments at
-// the end, or malformed offsets, which segment_locate_kernel reports) set
-// nothing.
-__global__ void segment_heads_kernel(const int64_t* offsets, int64_t num_segments, int64_t n,
-                                     uint32_t* bitmap) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < num_segments;
-         j += stride) {
-        const int64_t pos = offsets[j];
-        if (pos >= 0 && pos < n) atomicOr(&bitmap[pos >> 5], 1u << (pos & 31));
+// Head bitmap of a batched segmented scan: bit i of word i / 32 is set when
+// element i starts a segment.  Block b builds words [1024 b, 1024 b + 1024)
+// in shared memory and writes each once (no clearing pass, no global
+// atomics): it finds the first segment starting in its range with a 256-way
+// search (two rounds for 65,536 segments), then sets the bits of the segments
+// that start in the range.  Starts outside [0, n) set nothing.  The blocks
+// also check the offsets (monotone, offsets[0] = 0, offsets[S] = n) and record
+// GBSCAN_ERR_INVALID_ARG for malformed ones.  256 threads per block.
+constexpr int kBitmapBlockWords = 1024;
+
+__global__ void __launch_bounds__(256) segment_bitmap_kernel(const int64_t* offsets, int64_t num_segments,
+                                                             int64_t n, uint32_t* bitmap, int64_t words,
+                                                             Header* hdr) {
+    __shared__ uint32_t w[kBitmapBlockWords];
+    const int tid = threadIdx.x;
+    const int64_t w0 = static_cast<int64_t>(blockIdx.x) * kBitmapBlockWords;
+    const int64_t start = w0 * 32;
+    const int64_t end = start + 32ll * kBitmapBlockWords;
+    for (int i = tid; i < kBitmapBlockWords; i += 256) w[i] = 0u;
+    // j0 = the number of segments that start before `start`
+    int64_t lo = 0, len = num_segments;
+    while (len > 0) {
+        const int64_t step = (len + 255) / 256;
+        const int64_t idx = lo + static_cast<int64_t>(tid) * step;
+        const int below = (idx < lo + len && offsets[idx] < start) ? 1 : 0;
+        const int cnt = __syncthreads_count(below);
+        if (cnt == 0) break;
+        const int64_t nlo = lo + static_cast<int64_t>(cnt - 1) * step + 1;
+        const int64_t nhi = (lo + cnt * step) < (lo + len) ? (lo + cnt * step) : (lo + len);
+        lo = nlo;
+        len = nhi - nlo;
     }
+    __syncthreads();
+    for (int64_t j = lo + tid; j < num_segments; j += 256) {
+        const int64_t pos = offsets[j];
+        if (pos >= end) break;
+        if (pos >= start && pos < n) atomicOr(&w[(pos - start) >> 5], 1u << (pos & 31));
+    }
+    __syncthreads();
+    for (int i = tid; i < kBitmapBlockWords && w0 + i < words; i += 256) bitmap[w0 + i] = w[i];
+    // this block's share of the offset checks
+    bool bad = false;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * 256;
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * 256 + tid; j < num_segments; j += stride)
+        if (offsets[j] > offsets[j + 1]) bad = true;
+    if (blockIdx.x == 0 && tid == 0 && (offsets[0] != 0 || offsets[num_segments] != n)) bad = true;
+    if (bad) record_error(hdr, GBSCAN_ERR_INVALID_ARG, -1);
 }
 
 __global__ void set_debug_kernel(Header* hdr, uint32_t spin_limit_us, int64_t drop_tile,
@@ -287,26 +322,26 @@ gbscan_status scan_seg_impl(const Family& fam, const void* in, void* out, int64_
     const int64_t max_blocks = static_cast<int64_t>(sms > 0 ? sms : 1) * 8;
     if (blocks > max_blocks) blocks = max_blocks;
     if (v.partitioned) {
+        // the head bitmap (which also checks the offsets), then the scan
         const size_t boff = seg_bitmap_offset(n, esz), bbytes = seg_bitmap_bytes(n);
         if (ws_bytes < boff + bbytes) return GBSCAN_ERR_WORKSPACE;
         uint32_t* bitmap = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws) + boff);
-        if (cudaMemsetAsync(bitmap, 0, bbytes, stream) != cudaSuccess) return GBSCAN_ERR_CUDA;
-        int64_t hb = (num_segments + 255) / 256;
-        if (hb > max_blocks) hb = max_blocks;
-        if (hb < 1) hb = 1;
-        segment_heads_kernel<<<static_cast<unsigned>(hb), 256, 0, stream>>>(offsets, num_segments, n,
-                                                                            bitmap);
+        const int64_t words = static_cast<int64_t>(bbytes / 4);
+        const int64_t bb = (words + kBitmapBlockWords - 1) / kBitmapBlockWords;
+        segment_bitmap_kernel<<<static_cast<unsigned>(bb), 256, 0, stream>>>(offsets, num_segments, n,
+                                                                             bitmap, words, p.hdr);
+        if (cudaGetLastError() != cudaSuccess) return GBSCAN_ERR_CUDA;
         p.bitmap = bitmap;
         p.chunk_tiles = partition_chunk_tiles(v, esz);
         p.chunk_lag = partition_chunk_lag();
+        return from_cuda(v.partitioned(p, stream));
     }
-    // validates the offsets (and gives the single-pass kernel each tile's
-    // first segment)
+    // each tile's first segment for the single-pass kernel (also checks the
+    // offsets)
     segment_locate_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
         offsets, num_segments, n, v.tile, p.num_tiles, p.rec, p.hdr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return GBSCAN_ERR_CUDA;
-    if (v.partitioned) return from_cuda(v.partitioned(p, stream));
     return from_cuda(v.single_pass(p, stream));
 }
 

@@ -119,10 +119,9 @@ __device__ __forceinline__ void warp_inclusive_scan(bool& f, typename Op::Acc& v
 // (gf, gv).  Inclusive: y_j = prefix through item j; exclusive: before item j
 // (a segment head starts at 0).  Each output is the carry combined once with
 // the thread's local running sum.
-template <class Op, int ITEMS, int HEADS>
-__device__ __forceinline__ void thread_outputs(const typename Op::T (&x)[ITEMS], uint32_t hm,
-                                               typename Op::Acc gv, bool excl,
-                                               typename Op::T (&y)[ITEMS]) {
+template <class Op, int ITEMS, int HEADS, bool EXCL>
+__device__ __forceinline__ void thread_outputs_t(const typename Op::T (&x)[ITEMS], uint32_t hm,
+                                                 typename Op::Acc gv, typename Op::T (&y)[ITEMS]) {
     using T = typename Op::T;
     using Acc = typename Op::Acc;
     bool rf = false;
@@ -130,22 +129,26 @@ __device__ __forceinline__ void thread_outputs(const typename Op::T (&x)[ITEMS],
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const bool h = HEADS != kNoHeads && ((hm >> j) & 1u);
-        if (excl) {
-            if (h)
-                y[j] = T(0);
-            else if (rf)
-                y[j] = Op::output1(rv);
-            else
-                y[j] = Op::output(gv, rv);
-        }
+        if (EXCL) y[j] = h ? T(0) : (rf ? Op::output1(rv) : Op::output(gv, rv));
         if (h) {
             rv = Op::lift(x[j]);
             rf = true;
         } else {
             Op::accumulate(rv, x[j]);
         }
-        if (!excl) y[j] = rf ? Op::output1(rv) : Op::output(gv, rv);
+        if (!EXCL) y[j] = rf ? Op::output1(rv) : Op::output(gv, rv);
     }
+}
+
+template <class Op, int ITEMS, int HEADS>
+__device__ __forceinline__ void thread_outputs(const typename Op::T (&x)[ITEMS], uint32_t hm,
+                                               typename Op::Acc gv, bool excl,
+                                               typename Op::T (&y)[ITEMS]) {
+    // excl is the same for the whole launch: one branch, two straight loops
+    if (excl)
+        thread_outputs_t<Op, ITEMS, HEADS, true>(x, hm, gv, y);
+    else
+        thread_outputs_t<Op, ITEMS, HEADS, false>(x, hm, gv, y);
 }
 
 template <int NTHREADS>
