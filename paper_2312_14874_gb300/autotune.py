@@ -131,9 +131,11 @@ def tune(sizes_log2=(20, 22, 24, 26, 28, 30), write: bool = True, families=None,
         "bwd_f32": (torch.float32, lambda x, y, v: gb.backward(x.view(-1, 8192), out=y.view(-1, 8192),
                                                                 variant=v)),
     }
+    segmented = {"seg_i32": torch.int32, "seg_f32": torch.float32}
     if families:
         plain = {k: v for k, v in plain.items() if k in families}
         rowwise = {k: v for k, v in rowwise.items() if k in families}
+        segmented = {k: v for k, v in segmented.items() if k in families}
     key = gpu_key(dev)
     result: dict = {}
 
@@ -180,6 +182,30 @@ def tune(sizes_log2=(20, 22, 24, 26, 28, 30), write: bool = True, families=None,
                       ", ".join(f"v{v}={t * 1e3:.1f}us" for v, t in enumerate(times)) +
                       f" -> v{best}", flush=True)
             del x, y
+    for fam, dtype in segmented.items():
+        # segments with lengths log-uniform in [1, 2^16] (mean about 5900),
+        # as many as fill about 2^lg elements
+        import synth
+        result[fam] = {}
+        nv = gb.num_variants(dtype, _capi.KIND_SEGMENTED)
+        for lg in sizes(dtype):
+            if lg < 20:
+                continue
+            off = synth.segment_offsets(max(1, (1 << lg) // 5908), max_log2=16, seed=0)
+            n = int(off[-1])
+            o = torch.from_numpy(off).to(dev)
+            x = torch.zeros(n, dtype=dtype, device=dev)
+            y = torch.empty_like(x)
+            times = [_time_ms(lambda: gb.segmented(x, o, exclusive=True, out=y, variant=v))
+                     for v in range(nv)]
+            best = min(range(nv), key=lambda v: times[v])
+            bucket = max(0, math.ceil(math.log2(n)))
+            result[fam][str(bucket)] = best
+            if verbose:
+                print(f"[tune] {fam} n={n}: " +
+                      ", ".join(f"v{v}={t * 1e3:.1f}us" for v, t in enumerate(times)) +
+                      f" -> v{best}", flush=True)
+            del x, y, o
     if write:
         os.makedirs(TUNED_DIR, exist_ok=True)
         path = table_path(key)

@@ -243,14 +243,15 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
             bool f = hfl[q];
             Acc inc = v[q];
             warp_inclusive_scan<Op, HEADS>(f, inc, lane);
-            exf[q] = __shfl_up_sync(0xffffffffu, f ? 1 : 0, 1) != 0;
+            exf[q] = false;
+            if constexpr (HEADS != kNoHeads) exf[q] = __shfl_up_sync(0xffffffffu, f ? 1 : 0, 1) != 0;
             ex[q] = shfl_up_acc<Op>(inc, 1);
             if (lane == 0) {
                 exf[q] = false;
                 ex[q] = Op::identity();
             }
             v[q] = shfl_idx_acc<Op>(inc, 31);
-            hfl[q] = __shfl_sync(0xffffffffu, f ? 1 : 0, 31) != 0;
+            if constexpr (HEADS != kNoHeads) hfl[q] = __shfl_sync(0xffffffffu, f ? 1 : 0, 31) != 0;
         }
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -573,7 +574,8 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             bool wf = tf;
             Acc wv = tv;
             warp_inclusive_scan_w<Op, HEADS>(wh, wf, wv, lane);
-            bool xf = __shfl_up_sync(0xffffffffu, wf ? 1 : 0, 1) != 0;
+            bool xf = false;
+            if constexpr (HEADS != kNoHeads) xf = __shfl_up_sync(0xffffffffu, wf ? 1 : 0, 1) != 0;
             Acc ev = shfl_up_acc<Op>(wv, 1);
             if (lane == 0) {
                 xf = false;
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             }
             if (lane == 31) {
                 c.wtot_v[warp] = wv;
-                c.wtot_f[warp] = wf ? 1u : 0u;
+                if constexpr (HEADS != kNoHeads) c.wtot_f[warp] = wf ? 1u : 0u;
             }
             named_barrier_sync<CTHREADS>(1);
             // everything before this thread's first item: the tile's carry, the

@@ -104,13 +104,12 @@ __device__ __forceinline__ void warp_inclusive_scan(bool& f, typename Op::Acc& v
     using Acc = typename Op::Acc;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const bool fo = __shfl_up_sync(0xffffffffu, f ? 1 : 0, d) != 0;
         const Acc vo = shfl_up_acc<Op>(v, d);
-        if (lane >= d) {
-            if (HEADS != kNoHeads)
-                seg_combine<Op>(fo, vo, f, v);
-            else
-                v = Op::combine(vo, v);
+        if constexpr (HEADS != kNoHeads) {
+            const bool fo = __shfl_up_sync(0xffffffffu, f ? 1 : 0, d) != 0;
+            if (lane >= d) seg_combine<Op>(fo, vo, f, v);
+        } else {
+            if (lane >= d) v = Op::combine(vo, v);
         }
     }
 }
