@@ -290,6 +290,9 @@ def side_measurements(dev, peak) -> dict:
         v = pick("scan_i32", N, algo)
         rec(f"i32_2^30_{algo}", 8 * N, cuda_time_ms(
             lambda: gb.inclusive(x, out=y, workspace=ws, algo=algo, variant=v), reps)[0])
+    for op in ("max", "min"):
+        rec(f"i32_2^30_running_{op}_partitioned", 8 * N, cuda_time_ms(
+            lambda: gb.scan(x, out=y, op=op, algo="partitioned", variant=1, workspace=ws), reps)[0])
     rec("copy_torch_4GiB", 8 * N, cuda_time_ms(lambda: y.copy_(x), reps)[0])
     rec("copy_gbscan_4GiB", 8 * N, cuda_time_ms(lambda: gb.copy_(y, x), reps)[0])
     for algo in ("single_pass", "partitioned"):

@@ -77,7 +77,9 @@ typedef enum { GBSCAN_I32 = 0, GBSCAN_I64 = 1, GBSCAN_F32 = 2, GBSCAN_F64 = 3 } 
 typedef enum {
     GBSCAN_KIND_SCAN = 0,      /* one array, single-pass or two-pass */
     GBSCAN_KIND_SEGMENTED = 1, /* CSR segments, one persistent launch */
-    GBSCAN_KIND_ROWS = 2       /* rows x cols, along the last dim, forward or reverse */
+    GBSCAN_KIND_ROWS = 2,      /* rows x cols, along the last dim, forward or reverse */
+    GBSCAN_KIND_SCAN_MAX = 3,  /* one array, running maximum (int32, fp32) */
+    GBSCAN_KIND_SCAN_MIN = 4   /* one array, running minimum (int32, fp32) */
 } gbscan_kind;
 
 /* Bytes of workspace needed by any call of `kind` on `dtype` with n elements
@@ -184,6 +186,30 @@ gbscan_status scan_backward_f64(const double* grad_out, double* grad_in, int64_t
 /* Synchronises `stream`, returns the first device-side error recorded in the
  * workspace since the last call (GBSCAN_OK if none) and clears it. */
 gbscan_status scan_get_device_status(void* ws, cudaStream_t stream);
+
+/*
+ * Scans under another associative operator (Section 1 defines the prefix sum;
+ * the same scan exists for any associative operator, and + is the one the
+ * paper measures):
+ *   GBSCAN_OP_SUM  y_k = a_0 + ... + a_k    (the plain scans above)
+ *   GBSCAN_OP_MAX  y_k = max(a_0, ..., a_k) (running maximum)
+ *   GBSCAN_OP_MIN  y_k = min(a_0, ..., a_k) (running minimum)
+ * Exclusive scans start from the operator's identity (0; INT32_MIN or -inf for
+ * MAX; INT32_MAX or +inf for MIN).  fp32 MAX / MIN follow IEEE maxNum / minNum
+ * (a NaN operand yields the other operand).  Arguments, workspace
+ * (gbscan_workspace_size with GBSCAN_KIND_SCAN or the operator's kind),
+ * algorithms and errors as for the plain scans; variants per
+ * gbscan_num_variants(dtype, GBSCAN_KIND_SCAN_MAX / _MIN).  An unknown op
+ * returns GBSCAN_ERR_INVALID_ARG.
+ */
+typedef enum { GBSCAN_OP_SUM = 0, GBSCAN_OP_MAX = 1, GBSCAN_OP_MIN = 2 } gbscan_op;
+
+gbscan_status scan_op_i32(const int32_t* in, int32_t* out, int64_t n, gbscan_op op,
+                          int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo,
+                          int variant, cudaStream_t stream);
+gbscan_status scan_op_f32(const float* in, float* out, int64_t n, gbscan_op op, int exclusive,
+                          void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                          cudaStream_t stream);
 
 /* Test and tuning hooks, stored in the workspace header (not global state):
  *   spin_limit_us : bound of every wait on another tile, 0 = default (200 ms).

@@ -58,6 +58,10 @@ def _declare(lib):
         "oracle_rows_suffix_f32_ref": [vp, vp, i64, i64, ci],
         "oracle_rows_suffix_f64_ref": [vp, vp, i64, i64, ci],
         "oracle_rows_suffix_abs_f32": [vp, vp, i64, i64, ci],
+        "oracle_scan_max_i32": [vp, vp, i64, ci],
+        "oracle_scan_min_i32": [vp, vp, i64, ci],
+        "oracle_scan_max_f32": [vp, vp, i64, ci],
+        "oracle_scan_min_f32": [vp, vp, i64, ci],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -103,6 +107,22 @@ def scan_i64(a, exclusive: bool = False, lib=None) -> np.ndarray:
     a = _c(a, np.int64)
     y = np.empty_like(a)
     (lib or _load()).oracle_scan_i64(a.ctypes.data, y.ctypes.data, a.size, int(exclusive))
+    return y
+
+
+def scan_op(a, op: str, exclusive: bool = False, lib=None) -> np.ndarray:
+    """Running maximum or minimum (op "max" / "min") of int32 or float32 input."""
+    a = np.asarray(a)
+    if a.dtype == np.int32:
+        kind = "i32"
+    elif a.dtype == np.float32:
+        kind = "f32"
+    else:
+        raise TypeError("max / min scans take int32 or float32")
+    a = np.ascontiguousarray(a)
+    y = np.empty_like(a)
+    getattr(lib or _load(), f"oracle_scan_{op}_{kind}")(a.ctypes.data, y.ctypes.data, a.size,
+                                                          int(exclusive))
     return y
 
 

@@ -26,6 +26,12 @@
  *    segment start): segment s covers [offsets[s], offsets[s+1]).
  *  - The reverse (suffix) scan used by the gradient: y_i = sum_{k >= i} a_k
  *    (inclusive) or sum_{k > i} a_k (exclusive), per row.
+ *  - Other associative operators (Section 1 defines the scan for +; the same
+ *    definition holds for any associative operator): the running maximum and
+ *    minimum.  An exclusive scan starts from the operator's identity
+ *    (INT32_MIN / -inf for max, INT32_MAX / +inf for min).  fp32 max and min
+ *    are C's fmaxf / fminf (IEEE maxNum / minNum: a NaN operand yields the
+ *    other one).
  */
 #include <math.h>
 #include <stdint.h>
@@ -239,5 +245,43 @@ void oracle_rows_suffix_abs_f32(const float* a, double* y, int64_t rows, int64_t
                 yr[i] = acc.s + acc.c;
             }
         }
+    }
+}
+
+/* ---- running maximum / minimum (same definition, another operator) ------- */
+
+void oracle_scan_max_i32(const int32_t* a, int32_t* y, int64_t n, int exclusive) {
+    int32_t run = INT32_MIN;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) y[k] = run;
+        if (a[k] > run) run = a[k];
+        if (!exclusive) y[k] = run;
+    }
+}
+
+void oracle_scan_min_i32(const int32_t* a, int32_t* y, int64_t n, int exclusive) {
+    int32_t run = INT32_MAX;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) y[k] = run;
+        if (a[k] < run) run = a[k];
+        if (!exclusive) y[k] = run;
+    }
+}
+
+void oracle_scan_max_f32(const float* a, float* y, int64_t n, int exclusive) {
+    float run = -INFINITY;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) y[k] = run;
+        run = fmaxf(run, a[k]);
+        if (!exclusive) y[k] = run;
+    }
+}
+
+void oracle_scan_min_f32(const float* a, float* y, int64_t n, int exclusive) {
+    float run = INFINITY;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) y[k] = run;
+        run = fminf(run, a[k]);
+        if (!exclusive) y[k] = run;
     }
 }

@@ -11,6 +11,7 @@ rejected.
 
 Public API:
     inclusive(x), exclusive(x), scan(x, exclusive=...)  1-D int32/int64/float32/float64
+    scan(x, op="max" | "min")                           running max / min, int32/float32
     segmented(x, offsets, exclusive=...)                  CSR segments, int32/float32
     rows(x, exclusive=...), backward(g, exclusive=...)    along the last dim, float32/float64
     cumsum(x, dim=-1, exclusive=False)                    differentiable (autograd)
@@ -102,11 +103,16 @@ def _variant(kind: str, dtype_key: str, n: int, variant) -> int:
     return autotune.choose(kind, dtype_key, n)[1]
 
 
+_OPS = {"sum": _capi.OP_SUM, "max": _capi.OP_MAX, "min": _capi.OP_MIN}
+
+
 def scan(x: torch.Tensor, exclusive: bool = False, *, out: torch.Tensor | None = None,
          algo: str = "auto", compensated: bool = False, variant: int | None = None,
-         workspace: Workspace | None = None) -> torch.Tensor:
-    """Prefix sum of a contiguous CUDA tensor, flattened.  ``out`` may be ``x``
-    (in place).  ``compensated`` selects TwoSum-pair carries for float32."""
+         workspace: Workspace | None = None, op: str = "sum") -> torch.Tensor:
+    """Prefix sum (or, with ``op="max"`` / ``"min"``, running maximum / minimum
+    of int32 and float32) of a contiguous CUDA tensor, flattened.  ``out`` may
+    be ``x`` (in place).  ``compensated`` selects TwoSum-pair carries for
+    float32 sums."""
     _check_cuda(x, "x")
     if x.dtype not in _DTYPES:
         raise TypeError(f"unsupported dtype {x.dtype}")
@@ -122,6 +128,19 @@ def scan(x: torch.Tensor, exclusive: bool = False, *, out: torch.Tensor | None =
         return out
     if compensated and x.dtype != torch.float32:
         raise ValueError("compensated mode applies to float32")
+    if op not in _OPS:
+        raise ValueError(f"unknown op {op!r}")
+    if op != "sum":
+        if x.dtype not in (torch.int32, torch.float32) or compensated:
+            raise TypeError("max / min scans take int32 or float32 (no compensation)")
+        if algo not in _ALGOS:
+            raise ValueError(f"unknown algo {algo!r}")
+        v = 0 if variant is None else int(variant)
+        ws = workspace or _workspace_for(x.device, workspace_bytes(x.dtype, _capi.KIND_SCAN, n))
+        fn = _capi.lib().scan_op_i32 if key == "i32" else _capi.lib().scan_op_f32
+        _capi.check(fn(x.data_ptr(), out.data_ptr(), n, _OPS[op], int(exclusive), ws.ptr, ws.nbytes,
+                       _ALGOS[algo], v, _stream_handle(x.device)), "scan_op")
+        return out
     kind_key = "scan_" + key + ("c" if compensated else "")
     if algo not in _ALGOS:
         raise ValueError(f"unknown algo {algo!r}")

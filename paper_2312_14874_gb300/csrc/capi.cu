@@ -363,6 +363,14 @@ const Family* family_for(gbscan_dtype dt, gbscan_kind kind) {
         if (dt == GBSCAN_F32) return &family_rows_f32();
         if (dt == GBSCAN_F64) return &family_rows_f64();
         break;
+    case GBSCAN_KIND_SCAN_MAX:
+        if (dt == GBSCAN_I32) return &family_max_i32();
+        if (dt == GBSCAN_F32) return &family_max_f32();
+        break;
+    case GBSCAN_KIND_SCAN_MIN:
+        if (dt == GBSCAN_I32) return &family_min_i32();
+        if (dt == GBSCAN_F32) return &family_min_f32();
+        break;
     }
     return nullptr;
 }
@@ -383,7 +391,7 @@ gbscan_status gbscan_workspace_size(gbscan_dtype dtype, gbscan_kind kind, int64_
                                     int64_t num_segments, size_t* bytes) {
     if (bytes == nullptr || n < 0 || num_segments < 0 || !valid_dtype(dtype))
         return GBSCAN_ERR_INVALID_ARG;
-    if (kind < GBSCAN_KIND_SCAN || kind > GBSCAN_KIND_ROWS) return GBSCAN_ERR_INVALID_ARG;
+    if (kind < GBSCAN_KIND_SCAN || kind > GBSCAN_KIND_SCAN_MIN) return GBSCAN_ERR_INVALID_ARG;
     if (num_segments > INT32_MAX) return GBSCAN_ERR_UNSUPPORTED;
     const int tile = min_tile(dtype);
     if ((n + tile - 1) / tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
@@ -430,6 +438,30 @@ gbscan_status scan_exclusive_f32(const float* in, float* out, int64_t n, gbscan_
                                  void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                                  cudaStream_t stream) {
     return scan_f32_impl(in, out, n, mode, 1, ws, ws_bytes, algo, variant, stream);
+}
+
+gbscan_status scan_op_i32(const int32_t* in, int32_t* out, int64_t n, gbscan_op op,
+                          int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo,
+                          int variant, cudaStream_t stream) {
+    const Family* fam = op == GBSCAN_OP_SUM ? &family_scan_i32()
+                        : op == GBSCAN_OP_MAX ? &family_max_i32()
+                        : op == GBSCAN_OP_MIN ? &family_min_i32()
+                                              : nullptr;
+    if (!fam) return GBSCAN_ERR_INVALID_ARG;
+    return scan_flat(*fam, in, out, n, sizeof(int32_t), exclusive != 0, ws, ws_bytes, algo,
+                     variant, stream);
+}
+
+gbscan_status scan_op_f32(const float* in, float* out, int64_t n, gbscan_op op, int exclusive,
+                          void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                          cudaStream_t stream) {
+    const Family* fam = op == GBSCAN_OP_SUM ? &family_scan_f32()
+                        : op == GBSCAN_OP_MAX ? &family_max_f32()
+                        : op == GBSCAN_OP_MIN ? &family_min_f32()
+                                              : nullptr;
+    if (!fam) return GBSCAN_ERR_INVALID_ARG;
+    return scan_flat(*fam, in, out, n, sizeof(float), exclusive != 0, ws, ws_bytes, algo, variant,
+                     stream);
 }
 
 gbscan_status scan_segmented_batched_i32(const int32_t* in, int32_t* out, int64_t n,

@@ -348,6 +348,7 @@ __device__ __forceinline__ bool launch_aborted(const Header* hdr, uint32_t epoch
 
 struct OpI32 {
     using T = int32_t;
+    __device__ static T pad() { return T(0); }  // neutral element value
     using Acc = uint32_t;  // modular: two's complement wraparound
     using Bits = uint32_t;
     static constexpr bool kPacked = true;
@@ -363,6 +364,7 @@ struct OpI32 {
 
 struct OpI64 {
     using T = int64_t;
+    __device__ static T pad() { return T(0); }  // neutral element value
     using Acc = unsigned long long;
     using Bits = unsigned long long;
     static constexpr bool kPacked = false;
@@ -378,6 +380,7 @@ struct OpI64 {
 
 struct OpF32 {
     using T = float;
+    __device__ static T pad() { return T(0.0f); }  // neutral element value
     using Acc = float;
     using Bits = uint32_t;
     static constexpr bool kPacked = true;
@@ -393,6 +396,7 @@ struct OpF32 {
 
 struct OpF64 {
     using T = double;
+    __device__ static T pad() { return T(0.0); }  // neutral element value
     using Acc = double;
     using Bits = unsigned long long;
     static constexpr bool kPacked = false;
@@ -415,6 +419,74 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, ab), __fsub_rn(b, bb));
 }
 
+// Running maximum and minimum (the scan of any associative operator, of which
+// Section 1 takes +; identities -inf / +inf and INT32_MIN / INT32_MAX).  The
+// fp32 versions follow IEEE maxNum / minNum (fmaxf / fminf): a NaN operand
+// yields the other operand.
+struct OpMaxI32 {
+    using T = int32_t;
+    using Acc = int32_t;
+    using Bits = uint32_t;
+    static constexpr bool kPacked = true;
+    __device__ static T pad() { return INT32_MIN; }
+    __device__ static Acc identity() { return INT32_MIN; }
+    __device__ static Acc lift(T x) { return x; }
+    __device__ static Acc combine(Acc a, Acc b) { return a > b ? a : b; }
+    __device__ static void accumulate(Acc& r, T x) { r = r > x ? r : x; }
+    __device__ static T output(Acc c, Acc l) { return c > l ? c : l; }
+    __device__ static T output1(Acc v) { return v; }
+    __device__ static Bits to_bits(Acc a) { return static_cast<uint32_t>(a); }
+    __device__ static Acc from_bits(Bits b) { return static_cast<int32_t>(b); }
+};
+
+struct OpMinI32 {
+    using T = int32_t;
+    using Acc = int32_t;
+    using Bits = uint32_t;
+    static constexpr bool kPacked = true;
+    __device__ static T pad() { return INT32_MAX; }
+    __device__ static Acc identity() { return INT32_MAX; }
+    __device__ static Acc lift(T x) { return x; }
+    __device__ static Acc combine(Acc a, Acc b) { return a < b ? a : b; }
+    __device__ static void accumulate(Acc& r, T x) { r = r < x ? r : x; }
+    __device__ static T output(Acc c, Acc l) { return c < l ? c : l; }
+    __device__ static T output1(Acc v) { return v; }
+    __device__ static Bits to_bits(Acc a) { return static_cast<uint32_t>(a); }
+    __device__ static Acc from_bits(Bits b) { return static_cast<int32_t>(b); }
+};
+
+struct OpMaxF32 {
+    using T = float;
+    using Acc = float;
+    using Bits = uint32_t;
+    static constexpr bool kPacked = true;
+    __device__ static T pad() { return -__int_as_float(0x7f800000); }
+    __device__ static Acc identity() { return -__int_as_float(0x7f800000); }
+    __device__ static Acc lift(T x) { return x; }
+    __device__ static Acc combine(Acc a, Acc b) { return fmaxf(a, b); }
+    __device__ static void accumulate(Acc& r, T x) { r = fmaxf(r, x); }
+    __device__ static T output(Acc c, Acc l) { return fmaxf(c, l); }
+    __device__ static T output1(Acc v) { return v; }
+    __device__ static Bits to_bits(Acc a) { return __float_as_uint(a); }
+    __device__ static Acc from_bits(Bits b) { return __uint_as_float(b); }
+};
+
+struct OpMinF32 {
+    using T = float;
+    using Acc = float;
+    using Bits = uint32_t;
+    static constexpr bool kPacked = true;
+    __device__ static T pad() { return __int_as_float(0x7f800000); }
+    __device__ static Acc identity() { return __int_as_float(0x7f800000); }
+    __device__ static Acc lift(T x) { return x; }
+    __device__ static Acc combine(Acc a, Acc b) { return fminf(a, b); }
+    __device__ static void accumulate(Acc& r, T x) { r = fminf(r, x); }
+    __device__ static T output(Acc c, Acc l) { return fminf(c, l); }
+    __device__ static T output1(Acc v) { return v; }
+    __device__ static Bits to_bits(Acc a) { return __float_as_uint(a); }
+    __device__ static Acc from_bits(Bits b) { return __uint_as_float(b); }
+};
+
 // Compensated fp32: the accumulator is an unevaluated pair hi + lo, where hi
 // carries the rounded sum and lo the exact rounding errors of the additions into
 // hi (rounded once more when summed).  Per-thread running sums, warp and block
@@ -422,6 +494,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // output is rounded once, from the pair.
 struct OpF32C {
     using T = float;
+    __device__ static T pad() { return 0.0f; }  // neutral element value
     using Acc = float2;  // x = hi, y = lo
     using Bits = unsigned long long;
     static constexpr bool kPacked = false;

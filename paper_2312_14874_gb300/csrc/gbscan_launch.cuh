@@ -159,6 +159,10 @@ const Family& family_rows_f32();
 const Family& family_rows_f64();
 const Family& family_rows_rev_f32();
 const Family& family_rows_rev_f64();
+const Family& family_max_i32();
+const Family& family_min_i32();
+const Family& family_max_f32();
+const Family& family_min_f32();
 
 // Smallest tile (in elements) of any variant for an element size: sizes the
 // workspace so that every variant fits.

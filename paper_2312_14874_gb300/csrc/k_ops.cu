@@ -1,0 +1,23 @@
+// k_ops.cu — scans under other associative operators than +: running maximum
+// and running minimum of int32 and fp32 arrays (single-pass, two-pass and
+// partitioned, two launch shapes each).
+#include "gbscan_launch.cuh"
+
+namespace gbscan {
+
+#define GBSCAN_OP_FAMILY(FN, OP)                                                                \
+    static const Variant kVariants##OP[] = {                                                    \
+        GBSCAN_VARIANT_ALL(OP, 8, 20, 3, 8, 3, 2),                                              \
+        GBSCAN_VARIANT_ALL(OP, 8, 20, 4, 8, 2, 2),                                              \
+    };                                                                                          \
+    const Family& FN() {                                                                        \
+        static const Family f{2, kVariants##OP, &launch_scan_sums<OP>};                         \
+        return f;                                                                               \
+    }
+
+GBSCAN_OP_FAMILY(family_max_i32, OpMaxI32)
+GBSCAN_OP_FAMILY(family_min_i32, OpMinI32)
+GBSCAN_OP_FAMILY(family_max_f32, OpMaxF32)
+GBSCAN_OP_FAMILY(family_min_f32, OpMinF32)
+
+}  // namespace gbscan

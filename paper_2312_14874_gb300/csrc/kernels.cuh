@@ -297,7 +297,7 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
                 valid = valid_items<ITEMS>(cnt, tid);
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j)
-                    if (!((valid >> j) & 1u)) x[j] = T(0);
+                    if (!((valid >> j) & 1u)) x[j] = Op::pad();
             }
             uint32_t hm = 0;
             if constexpr (HEADS == kOffsetHeads) {
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(THREADS) two_pass_kernel(const Params p) {
             valid = valid_items<ITEMS>(cnt, tid);
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)
-                if (!((valid >> j) & 1u)) x[j] = T(0);
+                if (!((valid >> j) & 1u)) x[j] = Op::pad();
         }
         if (MODE == kScanOffset && refill_pending && tid == 0) {
             // the previous stage's store has had this block's whole load to

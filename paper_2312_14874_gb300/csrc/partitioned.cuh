@@ -469,7 +469,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 const uint32_t valid = valid_items<ITEMS>(cnt, tid);
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j)
-                    if (!((valid >> j) & 1u)) x[j] = T(0);
+                    if (!((valid >> j) & 1u)) x[j] = Op::pad();
             }
             uint32_t hm = 0;
             if constexpr (HEADS != kNoHeads) {

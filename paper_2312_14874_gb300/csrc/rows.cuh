@@ -153,7 +153,7 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) rowblock_kernel(const
                 valid = valid_items<ITEMS>(cnt, tid);
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j)
-                    if (!((valid >> j) & 1u)) x[j] = T(0);
+                    if (!((valid >> j) & 1u)) x[j] = Op::pad();
             }
             const uint32_t hm = row_heads<ITEMS, REVERSE>(tb, cnt, cols, tid) & valid;
             bool tf;

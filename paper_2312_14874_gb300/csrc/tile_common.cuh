@@ -128,7 +128,7 @@ __device__ __forceinline__ void thread_outputs_t(const typename Op::T (&x)[ITEMS
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const bool h = HEADS != kNoHeads && ((hm >> j) & 1u);
-        if (EXCL) y[j] = h ? T(0) : (rf ? Op::output1(rv) : Op::output(gv, rv));
+        if (EXCL) y[j] = h ? Op::output1(Op::identity()) : (rf ? Op::output1(rv) : Op::output(gv, rv));
         if (h) {
             rv = Op::lift(x[j]);
             rf = true;

@@ -11,6 +11,7 @@ against the oracle.
   CUDA-graph path: int32 U[0, 3] bit-exact, fp32 U[0, 1) within 1e-5.
 - [4096, 8192] fp32 N(0, 1): the row scan and its backward (suffix scan)
   within 1e-5.
+- int32 n = 2^30 running maximum and minimum, every algorithm, bit-exact.
 
 The measured errors are printed; with GBSCAN_PARITY_REPORT set to a path they
 are also written there as JSON.
@@ -64,6 +65,21 @@ def test_int32_2e30_every_algorithm(exclusive):
         assert gb.device_status() == 0, algo
         assert np.array_equal(y.cpu().numpy(), want), algo
     record(f"i32_2^30_{'exclusive' if exclusive else 'inclusive'}", "bit-exact: " + ", ".join(ALGOS))
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_int32_2e30_running_max_min(op):
+    n = 1 << 30
+    a = (synth.uniform_i32(n, 1 << 31, seed=0).astype(np.int64) - (1 << 30)).astype(np.int32)
+    want = oracle.scan_op(a, op)
+    x = torch.from_numpy(a).to(dev())
+    y = torch.empty_like(x)
+    for algo in ALGOS:
+        y.fill_(0)
+        gb.scan(x, out=y, op=op, algo=algo)
+        assert gb.device_status() == 0, algo
+        assert np.array_equal(y.cpu().numpy(), want), algo
+    record(f"i32_2^30_running_{op}", "bit-exact: " + ", ".join(ALGOS))
 
 
 def test_int64_2e29_every_algorithm():

@@ -285,3 +285,50 @@ def test_metric_zero_denominator():
     assert err == math.inf and k == 0
     err, k = oracle.max_rel_err([0.0, 1.0, 2.5], ref, [0.0, 1.0, 4.0])
     assert err == pytest.approx(0.125) and k == 2
+
+
+# ---- running maximum / minimum ------------------------------------------------
+
+def _brute_running(a, op, exclusive):
+    """O(n^2) definition: y_k = op over a[0..k] (exclusive: over a[0..k-1],
+    the identity when empty), NaNs skipped as IEEE maxNum / minNum do."""
+    if a.dtype == np.int32:
+        ident = np.iinfo(np.int32).min if op == "max" else np.iinfo(np.int32).max
+    else:
+        ident = -np.inf if op == "max" else np.inf
+    f = max if op == "max" else min
+    out = []
+    for k in range(a.size):
+        part = [v for v in a[: k if exclusive else k + 1].tolist() if v == v]
+        out.append(f(part) if part else ident)
+    return np.array(out, dtype=a.dtype)
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+@pytest.mark.parametrize("exclusive", [False, True])
+def test_running_max_min_brute_force(op, exclusive):
+    for n in (1, 2, 7, 33, 64):
+        a = (synth.uniform_i32(n, 1000, seed=n) - 500).astype(np.int32)
+        assert np.array_equal(oracle.scan_op(a, op, exclusive), _brute_running(a, op, exclusive))
+        f = synth.normal_f32(n, seed=n)
+        f[::5] = np.nan  # maxNum / minNum skip NaNs
+        assert np.array_equal(oracle.scan_op(f, op, exclusive), _brute_running(f, op, exclusive))
+
+
+def test_running_max_min_closed_forms_and_invariants():
+    k = np.arange(1000, dtype=np.int32)
+    assert np.array_equal(oracle.scan_op(k, "max"), k)            # increasing: itself
+    assert np.array_equal(oracle.scan_op(k[::-1].copy(), "max"), np.full(1000, 999, np.int32))
+    assert np.array_equal(oracle.scan_op(k[::-1].copy(), "min"), k[::-1])
+    assert oracle.scan_op(k, "max", True)[0] == np.iinfo(np.int32).min   # identity first
+    assert oracle.scan_op(k, "min", True)[0] == np.iinfo(np.int32).max
+    assert np.array_equal(oracle.scan_op(k, "max", True)[1:], k[:-1])   # exclusive = shift
+    a = (synth.uniform_i32(50000, 1 << 20, seed=3) - (1 << 19)).astype(np.int32)
+    y = oracle.scan_op(a, "max")
+    assert np.all(np.diff(y.astype(np.int64)) >= 0) and y[-1] == a.max()
+    assert np.all(np.isin(y, a))                    # every output is an input value
+    z = oracle.scan_op(a, "min")
+    assert np.all(np.diff(z.astype(np.int64)) <= 0) and z[-1] == a.min()
+    f = synth.normal_f32(50000, seed=4)
+    assert oracle.scan_op(f, "max")[-1] == f.max() and oracle.scan_op(f, "min")[-1] == f.min()
+    assert oracle.scan_op(f, "max", True)[0] == -np.inf

@@ -91,6 +91,17 @@ def pins_pass(lib) -> bool:
     checks.append(oracle.reduce_i32(i.astype(np.int32), lib=lib)
                   == np.int64(i.sum() % (1 << 32)).astype(np.uint32).view(np.int32))
     checks.append(oracle.reduce_i64(i, lib=lib) == i.sum())
+    # running max / min against their O(n^2) definition
+    r = (synth.uniform_i32(40, 100, seed=6) - 50).astype(np.int32)
+    rf = synth.normal_f32(40, seed=6)
+    for op, f in (("max", max), ("min", min)):
+        for excl in (False, True):
+            for arr, ident in ((r, np.iinfo(np.int32).min if op == "max" else np.iinfo(np.int32).max),
+                               (rf, -np.inf if op == "max" else np.inf)):
+                want = [f(arr[: k if excl else k + 1].tolist()) if (k or not excl) else ident
+                        for k in range(arr.size)]
+                checks.append(np.array_equal(oracle.scan_op(arr, op, excl, lib=lib),
+                                             np.array(want, dtype=arr.dtype)))
     return all(bool(c) for c in checks)
 
 
@@ -115,6 +126,12 @@ MUTANTS = {
                                 "int64_t b = offsets[s + 1], e = offsets[s + 1];\n        if (e > b) oracle_scan_f32_ref", 0),
     "suffix starts one early": ("for (int64_t i = cols - 1; i >= 0; --i) {", "for (int64_t i = cols - 2; i >= 0; --i) {", 0),
     "suffix f64 transposed index": ("const double* ar = a + r * cols;", "const double* ar = a + r;", 0),
+    "max exclusive writes after the update": (
+        "        if (exclusive) y[k] = run;\n        if (a[k] > run) run = a[k];",
+        "        if (a[k] > run) run = a[k];\n        if (exclusive) y[k] = run;", 0),
+    "min keeps the larger": ("if (a[k] < run) run = a[k];", "if (a[k] > run) run = a[k];", 0),
+    "f32 max starts from +inf": ("float run = -INFINITY;", "float run = INFINITY;", 0),
+    "f32 min uses fmaxf": ("run = fminf(run, a[k]);", "run = fmaxf(run, a[k]);", 0),
     "plain double exclusive shifted": ("y[k] = run;\n            run += (double)a[k];",
                                        "run += (double)a[k];\n            y[k] = run;", 0),
 }
