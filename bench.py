@@ -293,6 +293,13 @@ def side_measurements(dev, peak) -> dict:
     for op in ("max", "min"):
         rec(f"i32_2^30_running_{op}_partitioned", 8 * N, cuda_time_ms(
             lambda: gb.scan(x, out=y, op=op, algo="partitioned", variant=1, workspace=ws), reps)[0])
+    # stream compaction, half kept: bytes = payload + flags read, kept written
+    keep = torch.rand(N, device=dev) < 0.5
+    kept = int(keep.sum().item())
+    flags = keep.view(torch.uint8)
+    rec("compact_i32_2^30_half_kept", 5 * N + 4 * kept, cuda_time_ms(
+        lambda: gb.compact(x, flags, out=y, workspace=ws), reps)[0])
+    del keep, flags
     rec("copy_torch_4GiB", 8 * N, cuda_time_ms(lambda: y.copy_(x), reps)[0])
     rec("copy_gbscan_4GiB", 8 * N, cuda_time_ms(lambda: gb.copy_(y, x), reps)[0])
     for algo in ("single_pass", "partitioned"):

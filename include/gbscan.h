@@ -79,7 +79,8 @@ typedef enum {
     GBSCAN_KIND_SEGMENTED = 1, /* CSR segments, one persistent launch */
     GBSCAN_KIND_ROWS = 2,      /* rows x cols, along the last dim, forward or reverse */
     GBSCAN_KIND_SCAN_MAX = 3,  /* one array, running maximum (int32, fp32) */
-    GBSCAN_KIND_SCAN_MIN = 4   /* one array, running minimum (int32, fp32) */
+    GBSCAN_KIND_SCAN_MIN = 4,  /* one array, running minimum (int32, fp32) */
+    GBSCAN_KIND_COMPACT = 5    /* stream compaction (int32, fp32) */
 } gbscan_kind;
 
 /* Bytes of workspace needed by any call of `kind` on `dtype` with n elements
@@ -209,6 +210,28 @@ gbscan_status scan_op_i32(const int32_t* in, int32_t* out, int64_t n, gbscan_op 
                           int variant, cudaStream_t stream);
 gbscan_status scan_op_f32(const float* in, float* out, int64_t n, gbscan_op op, int exclusive,
                           void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                          cudaStream_t stream);
+
+/*
+ * Stream compaction, an application of the exclusive scan (Section 1 names
+ * stream compaction among the uses of prefix sums): the exclusive scan of the
+ * keep flags (1 where flags[i] != 0) gives each kept element its output
+ * position, so
+ *   out[j] = in[i_j] for the kept indices i_0 < i_1 < ..., j < *count,
+ *   *count = the number of kept elements (a DEVICE int64, written on `stream`).
+ * One launch: the partitioned scan of the flags fused with the gather
+ * (no flag prefix reaches memory).  in/out: device arrays of n 4-byte elements
+ * (copied bit for bit), not overlapping; flags: n device bytes; out must hold
+ * *count elements (n at most).  Workspace: gbscan_workspace_size(dtype,
+ * GBSCAN_KIND_COMPACT, n, 0).  n = 0 writes *count = 0.  Null pointers,
+ * overlap of in and out, or a count pointer not 8-byte aligned return
+ * GBSCAN_ERR_INVALID_ARG / GBSCAN_ERR_ALIGNMENT; device errors as for scans.
+ */
+gbscan_status compact_i32(const int32_t* in, const uint8_t* flags, int32_t* out, int64_t n,
+                          int64_t* count, void* ws, size_t ws_bytes, int variant,
+                          cudaStream_t stream);
+gbscan_status compact_f32(const float* in, const uint8_t* flags, float* out, int64_t n,
+                          int64_t* count, void* ws, size_t ws_bytes, int variant,
                           cudaStream_t stream);
 
 /* Test and tuning hooks, stored in the workspace header (not global state):

@@ -71,6 +71,8 @@ def _declare(lib):
     lib.oracle_reduce_i32.restype = ctypes.c_int32
     lib.oracle_reduce_i64.argtypes = [vp, i64]
     lib.oracle_reduce_i64.restype = ctypes.c_int64
+    lib.oracle_compact_u32.argtypes = [vp, vp, vp, i64]
+    lib.oracle_compact_u32.restype = ctypes.c_int64
     return lib
 
 
@@ -124,6 +126,19 @@ def scan_op(a, op: str, exclusive: bool = False, lib=None) -> np.ndarray:
     getattr(lib or _load(), f"oracle_scan_{op}_{kind}")(a.ctypes.data, y.ctypes.data, a.size,
                                                           int(exclusive))
     return y
+
+
+def compact(a, flags, lib=None) -> np.ndarray:
+    """The elements of a (4-byte dtype) whose flags are nonzero, in order."""
+    a = np.ascontiguousarray(a)
+    if a.dtype.itemsize != 4:
+        raise TypeError("compaction moves 4-byte elements")
+    f = np.ascontiguousarray(flags, dtype=np.uint8)
+    if f.size != a.size:
+        raise ValueError("flags must match a in length")
+    out = np.empty_like(a)
+    k = (lib or _load()).oracle_compact_u32(a.ctypes.data, f.ctypes.data, out.ctypes.data, a.size)
+    return out[:k]
 
 
 def reduce_i32(a, lib=None) -> int:

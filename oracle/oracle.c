@@ -32,6 +32,9 @@
  *    (INT32_MIN / -inf for max, INT32_MAX / +inf for min).  fp32 max and min
  *    are C's fmaxf / fminf (IEEE maxNum / minNum: a NaN operand yields the
  *    other one).
+ *  - Stream compaction (an application of the scan that Section 1 lists):
+ *    copy, in order, the elements whose keep flag is nonzero; the number kept
+ *    is the total of the flags.  Elements are moved as 4-byte words.
  */
 #include <math.h>
 #include <stdint.h>
@@ -284,4 +287,13 @@ void oracle_scan_min_f32(const float* a, float* y, int64_t n, int exclusive) {
         run = fminf(run, a[k]);
         if (!exclusive) y[k] = run;
     }
+}
+
+/* ---- stream compaction --------------------------------------------------- */
+
+int64_t oracle_compact_u32(const uint32_t* in, const uint8_t* flags, uint32_t* out, int64_t n) {
+    int64_t j = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (flags[i] != 0) out[j++] = in[i];
+    return j;
 }

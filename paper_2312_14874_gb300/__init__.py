@@ -12,6 +12,7 @@ rejected.
 Public API:
     inclusive(x), exclusive(x), scan(x, exclusive=...)  1-D int32/int64/float32/float64
     scan(x, op="max" | "min")                           running max / min, int32/float32
+    compact(x, flags)                                    stream compaction, int32/float32
     segmented(x, offsets, exclusive=...)                  CSR segments, int32/float32
     rows(x, exclusive=...), backward(g, exclusive=...)    along the last dim, float32/float64
     cumsum(x, dim=-1, exclusive=False)                    differentiable (autograd)
@@ -29,7 +30,7 @@ from ._capi import GbscanError
 __all__ = [
     "inclusive", "exclusive", "scan", "segmented", "rows", "backward", "cumsum",
     "device_status", "copy_", "Workspace", "workspace_bytes", "set_debug", "GbscanError",
-    "num_variants", "variant_info",
+    "num_variants", "variant_info", "compact",
 ]
 
 _DTYPES = {
@@ -170,6 +171,36 @@ def inclusive(x: torch.Tensor, **kw) -> torch.Tensor:
 
 def exclusive(x: torch.Tensor, **kw) -> torch.Tensor:
     return scan(x, True, **kw)
+
+
+def compact(x: torch.Tensor, flags: torch.Tensor, *, out: torch.Tensor | None = None,
+            variant: int = 0, workspace: Workspace | None = None):
+    """Stream compaction: the elements of ``x`` (int32 or float32, flattened)
+    whose ``flags`` (uint8 or bool, same length) are nonzero, in order.  One
+    launch (the scan of the flags fused with the gather).  Returns ``(out,
+    count)``: ``out`` holds x.numel() elements of which the first ``count``
+    (a 0-d int64 CUDA tensor, read it with ``.item()``) are the result."""
+    _check_cuda(x, "x")
+    _check_cuda(flags, "flags")
+    if x.dtype not in (torch.int32, torch.float32):
+        raise TypeError("compaction takes int32 or float32 values")
+    if flags.dtype == torch.bool:
+        flags = flags.view(torch.uint8)
+    if flags.dtype != torch.uint8 or flags.numel() != x.numel() or flags.device != x.device:
+        raise ValueError("flags must be uint8 or bool of x's length, on x's device")
+    n = x.numel()
+    if out is None:
+        out = torch.empty_like(x)
+    else:
+        _check_cuda(out, "out")
+        if out.dtype != x.dtype or out.numel() < n or out.device != x.device:
+            raise ValueError("out must match x in dtype and device and hold x.numel() elements")
+    count = torch.empty((), dtype=torch.int64, device=x.device)
+    ws = workspace or _workspace_for(x.device, workspace_bytes(x.dtype, _capi.KIND_COMPACT, n))
+    fn = _capi.lib().compact_i32 if x.dtype == torch.int32 else _capi.lib().compact_f32
+    _capi.check(fn(x.data_ptr(), flags.data_ptr(), out.data_ptr(), n, count.data_ptr(), ws.ptr,
+                   ws.nbytes, int(variant), _stream_handle(x.device)), "compact")
+    return out, count
 
 
 def segmented(x: torch.Tensor, offsets: torch.Tensor, exclusive: bool = False, *,

@@ -30,7 +30,7 @@ F32_PLAIN, F32_COMPENSATED = 0, 1
 # gbscan_dtype
 I32, I64, F32, F64 = 0, 1, 2, 3
 # gbscan_kind
-KIND_SCAN, KIND_SEGMENTED, KIND_ROWS, KIND_SCAN_MAX, KIND_SCAN_MIN = 0, 1, 2, 3, 4
+KIND_SCAN, KIND_SEGMENTED, KIND_ROWS, KIND_SCAN_MAX, KIND_SCAN_MIN, KIND_COMPACT = 0, 1, 2, 3, 4, 5
 # gbscan_op
 OP_SUM, OP_MAX, OP_MIN = 0, 1, 2
 
@@ -65,6 +65,8 @@ _SIGNATURES = {
     "scan_inclusive_i32_noalloc": [_vp, _vp, _i64, _vp],
     "scan_op_i32": [_vp, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _i32, _vp],
     "scan_op_f32": [_vp, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _i32, _vp],
+    "compact_i32": [_vp, _vp, _vp, _i64, _vp, _vp, _sz, _i32, _vp],
+    "compact_f32": [_vp, _vp, _vp, _i64, _vp, _vp, _sz, _i32, _vp],
 }
 _RESTYPE = {"gbscan_status_string": ctypes.c_char_p, "gbscan_num_variants": ctypes.c_int,
             "gbscan_abi_version": ctypes.c_int}

@@ -345,6 +345,30 @@ gbscan_status scan_seg_impl(const Family& fam, const void* in, void* out, int64_
     return from_cuda(v.single_pass(p, stream));
 }
 
+gbscan_status compact_impl(const void* in, const uint8_t* flags, void* out, int64_t n,
+                           int64_t* count, void* ws, size_t ws_bytes, int variant,
+                           cudaStream_t stream) {
+    const Family& fam = family_compact();
+    if (n < 0 || count == nullptr || variant < 0 || variant >= fam.num_variants)
+        return GBSCAN_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(count) % 8) return GBSCAN_ERR_ALIGNMENT;
+    cudaGetLastError();
+    if (n == 0) return from_cuda(cudaMemsetAsync(count, 0, sizeof(int64_t), stream));
+    if (flags == nullptr || in == out) return GBSCAN_ERR_INVALID_ARG;
+    gbscan_status st = check_io(in, out, n, 4);
+    if (st != GBSCAN_OK) return st;
+    const Variant& v = fam.variants[variant];
+    if ((n + v.tile - 1) / v.tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
+    st = check_ws(ws, ws_bytes, records_for(n, v.tile));
+    if (st != GBSCAN_OK) return st;
+    Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
+    p.flags = flags;
+    p.total_out = reinterpret_cast<unsigned long long*>(count);
+    p.chunk_tiles = partition_chunk_tiles(v, 4);
+    p.chunk_lag = partition_chunk_lag();
+    return from_cuda(v.partitioned(p, stream));
+}
+
 const Family* family_for(gbscan_dtype dt, gbscan_kind kind) {
     switch (kind) {
     case GBSCAN_KIND_SCAN:
@@ -371,6 +395,9 @@ const Family* family_for(gbscan_dtype dt, gbscan_kind kind) {
         if (dt == GBSCAN_I32) return &family_min_i32();
         if (dt == GBSCAN_F32) return &family_min_f32();
         break;
+    case GBSCAN_KIND_COMPACT:
+        if (dt == GBSCAN_I32 || dt == GBSCAN_F32) return &family_compact();
+        break;
     }
     return nullptr;
 }
@@ -391,7 +418,7 @@ gbscan_status gbscan_workspace_size(gbscan_dtype dtype, gbscan_kind kind, int64_
                                     int64_t num_segments, size_t* bytes) {
     if (bytes == nullptr || n < 0 || num_segments < 0 || !valid_dtype(dtype))
         return GBSCAN_ERR_INVALID_ARG;
-    if (kind < GBSCAN_KIND_SCAN || kind > GBSCAN_KIND_SCAN_MIN) return GBSCAN_ERR_INVALID_ARG;
+    if (kind < GBSCAN_KIND_SCAN || kind > GBSCAN_KIND_COMPACT) return GBSCAN_ERR_INVALID_ARG;
     if (num_segments > INT32_MAX) return GBSCAN_ERR_UNSUPPORTED;
     const int tile = min_tile(dtype);
     if ((n + tile - 1) / tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
@@ -438,6 +465,18 @@ gbscan_status scan_exclusive_f32(const float* in, float* out, int64_t n, gbscan_
                                  void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                                  cudaStream_t stream) {
     return scan_f32_impl(in, out, n, mode, 1, ws, ws_bytes, algo, variant, stream);
+}
+
+gbscan_status compact_i32(const int32_t* in, const uint8_t* flags, int32_t* out, int64_t n,
+                          int64_t* count, void* ws, size_t ws_bytes, int variant,
+                          cudaStream_t stream) {
+    return compact_impl(in, flags, out, n, count, ws, ws_bytes, variant, stream);
+}
+
+gbscan_status compact_f32(const float* in, const uint8_t* flags, float* out, int64_t n,
+                          int64_t* count, void* ws, size_t ws_bytes, int variant,
+                          cudaStream_t stream) {
+    return compact_impl(in, flags, out, n, count, ws, ws_bytes, variant, stream);
 }
 
 gbscan_status scan_op_i32(const int32_t* in, int32_t* out, int64_t n, gbscan_op op,

@@ -131,6 +131,8 @@ struct Params {
     int64_t cols;           // row kinds: row length
     int64_t chunk_tiles;    // partitioned scan: tiles per chunk
     int64_t chunk_lag;      // partitioned scan: chunk c is scanned beside the reduction of c + lag
+    const uint8_t* flags;   // compaction: keep flags (nonzero = keep)
+    unsigned long long* total_out; // compaction: the number kept (the last chunk prefix), or null
     int exclusive;
     int fast;               // in and out are 16-byte aligned: TMA path for full tiles
 };

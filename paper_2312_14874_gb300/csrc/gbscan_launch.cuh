@@ -7,6 +7,7 @@
 #include "kernels.cuh"
 #include "partitioned.cuh"
 #include "rows.cuh"
+#include "compact.cuh"
 
 namespace gbscan {
 
@@ -106,6 +107,13 @@ cudaError_t launch_rb(const Params& p, cudaStream_t stream) {
                              occ_cache, p, stream);
 }
 
+template <int CWARPS, int ITEMS, int STAGES, int MINB>
+cudaError_t launch_cp(const Params& p, cudaStream_t stream) {
+    static std::atomic<int> occ_cache[64];
+    return launch_persistent(compact_kernel<CWARPS, ITEMS, STAGES, MINB>, pt_threads<CWARPS>(),
+                             cp_smem_bytes<CWARPS, ITEMS, STAGES>(), occ_cache, p, stream);
+}
+
 template <class Op>
 cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStream_t stream) {
     scan_tile_sums_kernel<Op, 1024><<<1, 1024, 0, stream>>>(rec, num_tiles);
@@ -130,6 +138,14 @@ cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStr
     Variant {                                                                                  \
         (CW + 2) * 32, I, S, CW * 32 * I, nullptr, nullptr, nullptr,                           \
             &launch_pt<OP, CW, I, S, MB, kOffsetHeads>, kMaxChunkTiles                         \
+    }
+
+// Stream compaction (4-byte payloads): CW consumer warps x I items, S stages,
+// MB blocks per SM; threads counts the consumer, loader and scanner warps.
+#define GBSCAN_VARIANT_COMPACT(CW, I, S, MB)                                                    \
+    Variant {                                                                                  \
+        (CW + 2) * 32, I, S, CW * 32 * I, nullptr, nullptr, nullptr, &launch_cp<CW, I, S, MB>,   \
+            kMaxChunkTiles                                                                     \
     }
 
 // Row kinds: the chained kernel with row heads (any row length) and the
@@ -163,6 +179,7 @@ const Family& family_max_i32();
 const Family& family_min_i32();
 const Family& family_max_f32();
 const Family& family_min_f32();
+const Family& family_compact();
 
 // Smallest tile (in elements) of any variant for an element size: sizes the
 // workspace so that every variant fits.

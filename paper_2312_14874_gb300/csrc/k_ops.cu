@@ -1,6 +1,7 @@
 // k_ops.cu — scans under other associative operators than +: running maximum
 // and running minimum of int32 and fp32 arrays (single-pass, two-pass and
-// partitioned, two launch shapes each).
+// partitioned, two launch shapes each); and stream compaction, the scan of
+// keep flags fused with the gather it drives.
 #include "gbscan_launch.cuh"
 
 namespace gbscan {
@@ -19,5 +20,15 @@ GBSCAN_OP_FAMILY(family_max_i32, OpMaxI32)
 GBSCAN_OP_FAMILY(family_min_i32, OpMinI32)
 GBSCAN_OP_FAMILY(family_max_f32, OpMaxF32)
 GBSCAN_OP_FAMILY(family_min_f32, OpMinF32)
+
+static const Variant kCompact[] = {
+    GBSCAN_VARIANT_COMPACT(8, 20, 4, 2),
+    GBSCAN_VARIANT_COMPACT(8, 20, 3, 2),
+};
+
+const Family& family_compact() {
+    static const Family f{2, kCompact, nullptr};
+    return f;
+}
 
 }  // namespace gbscan

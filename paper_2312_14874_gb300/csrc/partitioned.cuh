@@ -308,6 +308,10 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
         else
             pv = Op::combine(e, carry);
         publish_words<Op>(rec_chunk(p.rec, ch, 2), rec_chunk(p.rec, ch, 3), epoch, kStateP, pf, pv);
+        // the last chunk's inclusive prefix is the total (stream compaction:
+        // the number of elements kept)
+        if (p.total_out != nullptr && first + nch == p.num_tiles)
+            *p.total_out = static_cast<unsigned long long>(Op::to_bits(pv));
     }
 }
 

@@ -12,6 +12,7 @@ against the oracle.
 - [4096, 8192] fp32 N(0, 1): the row scan and its backward (suffix scan)
   within 1e-5.
 - int32 n = 2^30 running maximum and minimum, every algorithm, bit-exact.
+- Stream compaction of int32 n = 2^30 with half the elements kept, bit-exact.
 
 The measured errors are printed; with GBSCAN_PARITY_REPORT set to a path they
 are also written there as JSON.
@@ -80,6 +81,19 @@ def test_int32_2e30_running_max_min(op):
         assert gb.device_status() == 0, algo
         assert np.array_equal(y.cpu().numpy(), want), algo
     record(f"i32_2^30_running_{op}", "bit-exact: " + ", ".join(ALGOS))
+
+
+def test_compact_int32_2e30_half_kept():
+    n = 1 << 30
+    a = synth.uniform_i32(n, 1 << 31, seed=1)
+    f = (synth.unit_f32(n, seed=2) < 0.5).astype(np.uint8)
+    want = oracle.compact(a, f)
+    out, cnt = gb.compact(torch.from_numpy(a).to(dev()), torch.from_numpy(f).to(dev()))
+    k = int(cnt.item())
+    assert k == want.size
+    assert np.array_equal(out[:k].cpu().numpy(), want)
+    assert gb.device_status() == 0
+    record("compact_i32_2^30_half_kept", f"bit-exact, kept {k}")
 
 
 def test_int64_2e29_every_algorithm():

@@ -332,3 +332,17 @@ def test_running_max_min_closed_forms_and_invariants():
     f = synth.normal_f32(50000, seed=4)
     assert oracle.scan_op(f, "max")[-1] == f.max() and oracle.scan_op(f, "min")[-1] == f.min()
     assert oracle.scan_op(f, "max", True)[0] == -np.inf
+
+
+# ---- stream compaction ----------------------------------------------------------
+
+def test_compaction_definition():
+    for n in (1, 5, 64, 1000):
+        a = synth.uniform_i32(n, 1 << 20, seed=n)
+        f = (synth.uniform_i32(n, 3, seed=n + 1)).astype(np.uint8)  # 0, 1, 2: nonzero keeps
+        want = np.array([a[i] for i in range(n) if f[i] != 0], dtype=np.int32)
+        got = oracle.compact(a, f)
+        assert np.array_equal(got, want) and got.size == int(np.count_nonzero(f))
+    x = synth.normal_f32(777, seed=2)
+    assert np.array_equal(oracle.compact(x, np.ones(777, np.uint8)).view(np.uint32), x.view(np.uint32))
+    assert oracle.compact(x, np.zeros(777, np.uint8)).size == 0

@@ -102,6 +102,10 @@ def pins_pass(lib) -> bool:
                         for k in range(arr.size)]
                 checks.append(np.array_equal(oracle.scan_op(arr, op, excl, lib=lib),
                                              np.array(want, dtype=arr.dtype)))
+    cf = (synth.uniform_i32(50, 2, seed=7)).astype(np.uint8)
+    cv = synth.uniform_i32(50, 1000, seed=8)
+    checks.append(np.array_equal(oracle.compact(cv, cf, lib=lib),
+                                 np.array([cv[i] for i in range(50) if cf[i]], np.int32)))
     return all(bool(c) for c in checks)
 
 
@@ -132,6 +136,9 @@ MUTANTS = {
     "min keeps the larger": ("if (a[k] < run) run = a[k];", "if (a[k] > run) run = a[k];", 0),
     "f32 max starts from +inf": ("float run = -INFINITY;", "float run = INFINITY;", 0),
     "f32 min uses fmaxf": ("run = fminf(run, a[k]);", "run = fmaxf(run, a[k]);", 0),
+    "compaction keeps the dropped": ("if (flags[i] != 0) out[j++] = in[i];", "if (flags[i] == 0) out[j++] = in[i];", 0),
+    "compaction writes in place of the input index": ("if (flags[i] != 0) out[j++] = in[i];",
+                                                      "if (flags[i] != 0) { out[j] = in[j]; j++; }", 0),
     "plain double exclusive shifted": ("y[k] = run;\n            run += (double)a[k];",
                                        "run += (double)a[k];\n            y[k] = run;", 0),
 }
