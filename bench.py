@@ -431,17 +431,16 @@ def main(argv=None) -> int:
     ms_per_step = secs_max * 1e3 / args.steps
     achieved = BYTES_PER_STEP / (avg_launch_ms * 1e-3) / 1e9
 
-    # end to end through the public API: pinned host input -> device -> scan ->
-    # pinned host output, every step
+    # end to end through the C ABI with host buffers (scan_inclusive_i32_host):
+    # pinned host input -> device -> scan -> pinned host output, every step,
+    # uploads, scans and downloads of 64 MiB pieces overlapping
     e2e = None
     if not args.no_e2e:
         h_out = torch.empty(N, dtype=torch.int32, pin_memory=True)
         e2e_steps = 3
 
         def e2e_step():
-            x.copy_(h_in, non_blocking=True)
-            gb.inclusive(x, out=y, workspace=ws, variant=variant, algo=algo)
-            h_out.copy_(y, non_blocking=True)
+            gb.inclusive_host(h_in, h_out, d_buf=x, workspace=ws)
 
         e2e_step()
         torch.cuda.synchronize(dev)
@@ -453,6 +452,8 @@ def main(argv=None) -> int:
             e2e_step()
         b.record(stream)
         b.synchronize()
+        if int(h_out[-1].item()) % (1 << 32) != total:
+            raise RuntimeError("end-to-end result failed the last == total check")
         e2e_secs = max_over_ranks(a.elapsed_time(b) / 1e3 / e2e_steps, dev)
         e2e = {"value": round(aggregate(BYTES_PER_STEP, e2e_secs, world), 3), "unit": "GB/s",
                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,

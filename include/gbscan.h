@@ -234,6 +234,29 @@ gbscan_status compact_f32(const float* in, const uint8_t* flags, float* out, int
                           int64_t* count, void* ws, size_t ws_bytes, int variant,
                           cudaStream_t stream);
 
+/*
+ * End to end from host memory: the inclusive int32 scan (Section 1) of a HOST
+ * array into a HOST array, through a device staging buffer.
+ *   h_in, h_out : host arrays of n elements (pinned memory lets the copies run
+ *                 asynchronously and overlap; pageable memory works, slower).
+ *   d_buf       : device buffer of d_elems int32 elements, 16-byte aligned.  With
+ *                 d_elems >= n the whole array stays resident; otherwise it is a
+ *                 ring of at least two slots (d_elems >= 8192 required).
+ *   ws          : workspace for a plain int32 scan of one piece (at most 16 Mi
+ *                 elements: gbscan_workspace_size(I32, SCAN, min(n, 16Mi), 0)).
+ * The array moves in pieces of up to 16 Mi elements: the upload of piece k
+ * (on `stream`), its in-place partitioned scan continuing from the pieces
+ * before it (the previous piece's last prefix, kept in the workspace header),
+ * and its download run on three streams, so uploads, scans and downloads of
+ * different pieces overlap.  Asynchronous: `stream` reaches the end of the
+ * last download; h_out is valid after synchronising it.  Errors: null
+ * pointers, negative sizes or a too small ring return GBSCAN_ERR_INVALID_ARG;
+ * an unaligned d_buf GBSCAN_ERR_ALIGNMENT; a failed CUDA call GBSCAN_ERR_CUDA.
+ */
+gbscan_status scan_inclusive_i32_host(const int32_t* h_in, int32_t* h_out, int64_t n,
+                                      int32_t* d_buf, int64_t d_elems, void* ws, size_t ws_bytes,
+                                      cudaStream_t stream);
+
 /* Test and tuning hooks, stored in the workspace header (not global state):
  *   spin_limit_us : bound of every wait on another tile, 0 = default (200 ms).
  *   drop_tile     : a tile index whose status is never published (-1 = none):

@@ -13,6 +13,7 @@ Public API:
     inclusive(x), exclusive(x), scan(x, exclusive=...)  1-D int32/int64/float32/float64
     scan(x, op="max" | "min")                           running max / min, int32/float32
     compact(x, flags)                                    stream compaction, int32/float32
+    inclusive_host(h_in)                                 int32 scan of a host array, pipelined
     segmented(x, offsets, exclusive=...)                  CSR segments, int32/float32
     rows(x, exclusive=...), backward(g, exclusive=...)    along the last dim, float32/float64
     cumsum(x, dim=-1, exclusive=False)                    differentiable (autograd)
@@ -30,7 +31,7 @@ from ._capi import GbscanError
 __all__ = [
     "inclusive", "exclusive", "scan", "segmented", "rows", "backward", "cumsum",
     "device_status", "copy_", "Workspace", "workspace_bytes", "set_debug", "GbscanError",
-    "num_variants", "variant_info", "compact",
+    "num_variants", "variant_info", "compact", "inclusive_host",
 ]
 
 _DTYPES = {
@@ -171,6 +172,39 @@ def inclusive(x: torch.Tensor, **kw) -> torch.Tensor:
 
 def exclusive(x: torch.Tensor, **kw) -> torch.Tensor:
     return scan(x, True, **kw)
+
+
+def inclusive_host(h_in: torch.Tensor, h_out: torch.Tensor | None = None, *,
+                   d_buf: torch.Tensor | None = None, device=None,
+                   workspace: Workspace | None = None) -> torch.Tensor:
+    """Inclusive int32 scan of a HOST tensor into a host tensor, pipelined
+    through the GPU (uploads, scans and downloads of 64 MiB pieces overlap).
+    ``d_buf`` is the device staging buffer (default: 4 pieces).  Asynchronous
+    on the device's current stream: synchronise before reading ``h_out``."""
+    if not isinstance(h_in, torch.Tensor) or h_in.is_cuda or h_in.dtype != torch.int32:
+        raise TypeError("h_in must be an int32 CPU tensor")
+    if not h_in.is_contiguous():
+        raise ValueError("h_in must be contiguous")
+    n = h_in.numel()
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+        else torch.device(device)
+    if h_out is None:
+        h_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    if h_out.is_cuda or h_out.dtype != torch.int32 or h_out.numel() != n or not h_out.is_contiguous():
+        raise ValueError("h_out must be a contiguous int32 CPU tensor of h_in's length")
+    if n == 0:
+        return h_out
+    piece = 16 << 20
+    if d_buf is None:
+        d_buf = torch.empty(min(n, 4 * piece), dtype=torch.int32, device=device)
+    _check_cuda(d_buf, "d_buf")
+    ws = workspace or _workspace_for(
+        device, workspace_bytes(torch.int32, _capi.KIND_SCAN, min(n, piece)))
+    _capi.check(_capi.lib().scan_inclusive_i32_host(h_in.data_ptr(), h_out.data_ptr(), n,
+                                                     d_buf.data_ptr(), d_buf.numel(), ws.ptr,
+                                                     ws.nbytes, _stream_handle(device)),
+                "scan_inclusive_i32_host")
+    return h_out
 
 
 def compact(x: torch.Tensor, flags: torch.Tensor, *, out: torch.Tensor | None = None,

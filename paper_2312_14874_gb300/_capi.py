@@ -67,6 +67,7 @@ _SIGNATURES = {
     "scan_op_f32": [_vp, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _i32, _vp],
     "compact_i32": [_vp, _vp, _vp, _i64, _vp, _vp, _sz, _i32, _vp],
     "compact_f32": [_vp, _vp, _vp, _i64, _vp, _vp, _sz, _i32, _vp],
+    "scan_inclusive_i32_host": [_vp, _vp, _i64, _vp, _i64, _vp, _sz, _vp],
 }
 _RESTYPE = {"gbscan_status_string": ctypes.c_char_p, "gbscan_num_variants": ctypes.c_int,
             "gbscan_abi_version": ctypes.c_int}

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "gbscan_launch.cuh"
 
@@ -465,6 +466,94 @@ gbscan_status scan_exclusive_f32(const float* in, float* out, int64_t n, gbscan_
                                  void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                                  cudaStream_t stream) {
     return scan_f32_impl(in, out, n, mode, 1, ws, ws_bytes, algo, variant, stream);
+}
+
+// Pieces of the host pipeline: at most 16 Mi elements (64 MiB) each.
+constexpr int64_t kHostPieceElems = 16ll << 20;
+
+gbscan_status scan_inclusive_i32_host(const int32_t* h_in, int32_t* h_out, int64_t n,
+                                      int32_t* d_buf, int64_t d_elems, void* ws, size_t ws_bytes,
+                                      cudaStream_t stream) {
+    if (n < 0 || d_elems < 0) return GBSCAN_ERR_INVALID_ARG;
+    if (n == 0) return GBSCAN_OK;
+    if (h_in == nullptr || h_out == nullptr || d_buf == nullptr) return GBSCAN_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_buf) % 16) return GBSCAN_ERR_ALIGNMENT;
+    int64_t m = n < kHostPieceElems ? n : kHostPieceElems;
+    if (d_elems < n) {
+        // a ring of at least two slots
+        if (m > d_elems / 2) m = d_elems / 2;
+        m &= ~int64_t(3);  // slots stay 16-byte aligned
+        if (m < 4096) return GBSCAN_ERR_INVALID_ARG;
+    }
+    const int64_t P = (n + m - 1) / m;
+    int64_t R = d_elems / m;
+    if (R > P) R = P;
+    const Family& fam = family_scan_i32();
+    const Variant& v = fam.variants[1];  // the partitioned shape tuned for large int32 scans
+    gbscan_status st = check_ws(ws, ws_bytes, records_for(m, v.tile));
+    if (st != GBSCAN_OK) return st;
+    Header* hdr = static_cast<Header*>(ws);
+    cudaGetLastError();
+
+    cudaStream_t s_cmp = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> evs;
+    auto event = [&]() -> cudaEvent_t {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        evs.push_back(e);
+        return e;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&s_cmp, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking);
+    std::vector<cudaEvent_t> ev_cmp(P, nullptr), ev_out(P, nullptr);
+    cudaEvent_t ev_start = event();
+    if (e == cudaSuccess && !ev_start) e = cudaErrorMemoryAllocation;
+    // the internal streams start after the work already queued on `stream`
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cmp, ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_start, 0);
+    for (int64_t k = 0; k < P && e == cudaSuccess; ++k) {
+        const int64_t off = k * m;
+        const int64_t len = (n - off) < m ? (n - off) : m;
+        int32_t* slot = d_buf + (k % R) * m;
+        // upload (on `stream`) once the slot's previous piece is downloaded
+        if (k >= R) e = cudaStreamWaitEvent(stream, ev_out[k - R], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(slot, h_in + off, static_cast<size_t>(len) * 4, cudaMemcpyHostToDevice,
+                                stream);
+        cudaEvent_t ev_in = event();
+        if (e == cudaSuccess && !ev_in) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in, stream);
+        // scan in place, continuing from the pieces before it
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cmp, ev_in, 0);
+        if (e == cudaSuccess) {
+            Params p = make_params(slot, slot, len, v.tile, ws, ws_bytes);
+            p.chunk_tiles = partition_chunk_tiles(v, 4);
+            p.chunk_lag = partition_chunk_lag();
+            p.carry_in = k > 0 ? &hdr->host_carry : nullptr;
+            e = v.partitioned(p, s_cmp);
+        }
+        // its last prefix carries into the next piece
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&hdr->host_carry, slot + len - 1, 4, cudaMemcpyDeviceToDevice, s_cmp);
+        ev_cmp[k] = event();
+        if (e == cudaSuccess && !ev_cmp[k]) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaEventRecord(ev_cmp[k], s_cmp);
+        // download
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_cmp[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out + off, slot, static_cast<size_t>(len) * 4, cudaMemcpyDeviceToHost,
+                                s_out);
+        ev_out[k] = event();
+        if (e == cudaSuccess && !ev_out[k]) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaEventRecord(ev_out[k], s_out);
+    }
+    // `stream` continues once every download is done
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_out[P - 1], 0);
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+    if (s_cmp) cudaStreamDestroy(s_cmp);
+    if (s_out) cudaStreamDestroy(s_out);
+    return from_cuda(e);
 }
 
 gbscan_status compact_i32(const int32_t* in, const uint8_t* flags, int32_t* out, int64_t n,

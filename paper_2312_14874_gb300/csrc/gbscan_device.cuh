@@ -59,7 +59,9 @@ struct alignas(256) Header {
     uint32_t delay_ns_max;  // race-stress sleeps before publishing, 0 = off
     int64_t drop_tile_plus1;// debug: this tile (minus one) never publishes, 0 = none
     uint32_t abort_epoch;   // epoch of a launch in which a bounded wait ran out
-    uint32_t reserved[53];
+    uint32_t reserved0;
+    int64_t host_carry;     // host pipeline: the inclusive total of the pieces scanned so far
+    uint32_t reserved[50];
 };
 static_assert(sizeof(Header) == 256, "header size");
 
@@ -133,6 +135,7 @@ struct Params {
     int64_t chunk_lag;      // partitioned scan: chunk c is scanned beside the reduction of c + lag
     const uint8_t* flags;   // compaction: keep flags (nonzero = keep)
     unsigned long long* total_out; // compaction: the number kept (the last chunk prefix), or null
+    const void* carry_in;   // partitioned scan: one element (device) folded in before element 0, or null
     int exclusive;
     int fast;               // in and out are 16-byte aligned: TMA path for full tiles
 };

@@ -282,7 +282,10 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
         }
         Acc e = Op::identity();
         bool ef = false;
-        if (ch > 0) {
+        if (ch == 0 && p.carry_in != nullptr) {
+            // a scan that continues an earlier one: everything before element 0
+            e = Op::lift(*static_cast<const typename Op::T*>(p.carry_in));
+        } else if (ch > 0) {
             uint32_t st = kStateX;
             const uint64_t t0 = global_timer_ns();
             while (true) {
