@@ -101,10 +101,10 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
  *   ws        : zeroed workspace of ws_bytes >= gbscan_workspace_size(dtype, SCAN, n, 0).
  *   algo      : GBSCAN_ALGO_SINGLE_PASS (one launch), TWO_PASS (three launches:
  *               tile reduce, one-block scan of the tile sums, scan with offsets),
- *               PARTITIONED (one launch: the array is cut into chunks of about 12 MiB,
+ *               PARTITIONED (one launch: the array is cut into chunks of about 8 MiB,
  *               environment variable GBSCAN_CHUNK_BYTES; each chunk is reduced tile by
  *               tile, its tile sums are scanned, and it is scanned a second time while
- *               still in L2, overlapped with the reduction of the chunk three ahead,
+ *               still in L2, overlapped with the reduction of the chunk four ahead,
  *               GBSCAN_CHUNK_LAG), or AUTO (PARTITIONED for inputs of 128 MiB or
  *               more, TWO_PASS below and for compensated fp32 at any size: the
  *               fastest choice measured on GB300).

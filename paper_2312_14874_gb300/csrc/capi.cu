@@ -193,8 +193,8 @@ Params make_params(const void* in, void* out, int64_t n, int tile, void* ws, siz
 }
 
 // Tiles per chunk of the partitioned scan: about GBSCAN_CHUNK_BYTES of input
-// (default 12 MiB: with the default three-chunk lag, four chunks of input,
-// 48 MiB, are live in the 129 MB L2 at a time, next to the streaming stores),
+// (default 8 MiB: with the default four-chunk lag, five chunks of input,
+// 40 MiB, are live in the 129 MB L2 at a time, next to the streaming stores),
 // at least 16 tiles.
 static long long env_cached(std::atomic<long long>& cache, const char* name, long long dflt) {
     long long v = cache.load(std::memory_order_relaxed);
@@ -218,19 +218,19 @@ constexpr uint64_t kAutoPartitionedBytes = 128ull << 20;
 
 int64_t partition_chunk_tiles(const Variant& v, size_t esz) {
     static std::atomic<long long> bytes_cache{0};
-    const long long bytes = env_cached(bytes_cache, "GBSCAN_CHUNK_BYTES", 12ll << 20);
+    const long long bytes = env_cached(bytes_cache, "GBSCAN_CHUNK_BYTES", 8ll << 20);
     int64_t k = bytes / (static_cast<long long>(v.tile) * static_cast<long long>(esz));
     if (k < kGroup) k = kGroup;
     if (k > v.max_chunk_tiles) k = v.max_chunk_tiles;
     return k;
 }
 
-// Chunks between a chunk's reduction and its scan (GBSCAN_CHUNK_LAG, default 3,
+// Chunks between a chunk's reduction and its scan (GBSCAN_CHUNK_LAG, default 4,
 // at most 8): the slack the chunk scanner has to publish a chunk's offsets
 // before the chunk's second pass starts.
 int64_t partition_chunk_lag() {
     static std::atomic<long long> lag_cache{0};
-    const long long lag = env_cached(lag_cache, "GBSCAN_CHUNK_LAG", 3);
+    const long long lag = env_cached(lag_cache, "GBSCAN_CHUNK_LAG", 4);
     return lag > 8 ? 8 : lag;
 }
 

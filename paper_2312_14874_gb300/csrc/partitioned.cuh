@@ -5,29 +5,34 @@
 // partition before moving on, so that the second pass reads from cache instead
 // of memory; keep two `sums` arrays so that the second pass of iteration k
 // overlaps the first pass of iteration k+1 (Section 2.2.1).  Here the cache is
-// the GPU's L2 (129 MB): a chunk is a run of chunk_tiles tiles of a few tens of
-// MB, and one persistent launch processes a work list in which the second pass
-// (scan) of chunk c is interleaved with the first pass (reduce, "Accumulate")
-// of chunk c+lag (by default a lag of two chunks, so that the scan of chunk c's
-// tile sums has a whole slot of work to finish in):
+// the GPU's L2 (129 MB): a chunk is a run of chunk_tiles tiles of a few MB (8 MiB
+// by default), and one persistent launch processes a work list in which the
+// second pass (scan) of chunk c is interleaved with the first pass (reduce,
+// "Accumulate") of chunk c+lag (4 by default: the scan of chunk c's tile sums
+// has several slots of work to finish in), e.g. with a lag of two:
 //
 //   R(0) R(1) | S(0) R(2) S(0) R(2) ... | S(1) R(3) ... | ... | S(C-1)
 //
 // R item:  TMA-load the tile with L2 evict-last priority (it will be read again),
 //          sum it, publish the sum in the tile's status word.  The last R item of
-//          a chunk then scans the chunk's tile sums (the per-partition `sums`
-//          array): waits until all are published, publishes each tile's
-//          exclusive offset within the chunk in the tile's status word, and
-//          chains the chunk prefixes (E, P) from the previous chunk.
+//          a chunk hands the chunk to its block's scanner warp, which scans the
+//          chunk's tile sums (the per-partition `sums` array): waits until all
+//          are published, publishes each tile's exclusive offset within the
+//          chunk in the tile's status word, and chains the chunk prefixes (E, P)
+//          from the previous chunk.
 // S item:  TMA-load the tile again (from L2, evict-first) together with the two
 //          status words it needs (its in-chunk offset and the chunk prefix E),
 //          which are self-validating (epoch-tagged), so no global round trip is
 //          left on the scan's path; scan, store with a TMA bulk store.
+// The scanner warp runs beside the block's consumers, so no item waits behind
+// a chunk scan.
 //
 // There is no per-tile dependency chain: a tile's S item waits only for its
-// chunk's prefix, published once per chunk, which is why this scheme reaches
-// copy bandwidth where a per-tile chained scan is bound by status round trips.
-// Plain (unsegmented, forward) scans only.
+// chunk's prefix, published once per chunk, which is why this scheme comes
+// close to copy bandwidth where a per-tile chained scan is bound by status
+// round trips.  Forward scans, plain or segmented (HEADS = kOffsetHeads: a
+// head bitmap travels with each tile and the chunk scan uses the segmented
+// operator).
 #pragma once
 
 #include "tile_common.cuh"

@@ -249,7 +249,7 @@ def test_partitioned_many_small_chunks(tmp_path, lag):
 
 
 def test_partitioned_multi_chunk_default_size():
-    """Default 24 MiB chunks: an array of several chunks plus a ragged tail."""
+    """Default chunks (8 MiB): an array of several chunks plus a ragged tail."""
     n = 7 * 1228 * 5120 + 12345
     a = synth.uniform_i32(n, 256, seed=11)
     x = to_dev(a)
