@@ -365,7 +365,8 @@ gbscan_status compact_impl(const void* in, const uint8_t* flags, void* out, int6
     Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
     p.flags = flags;
     p.total_out = reinterpret_cast<unsigned long long*>(count);
-    p.chunk_tiles = partition_chunk_tiles(v, 4);
+    // whole R groups per chunk
+    p.chunk_tiles = (partition_chunk_tiles(v, 4) + kCpGroup - 1) / kCpGroup * kCpGroup;
     p.chunk_lag = partition_chunk_lag();
     return from_cuda(v.partitioned(p, stream));
 }

@@ -3,11 +3,13 @@
 //
 // The exclusive scan of the 0/1 keep flags (Section 1's definition over the
 // flags) gives every kept element its position in the output.  The scan is the
-// partitioned one (Section 2.2): a work list of reduce items R (count the kept
-// elements of a tile from its flags alone, flags read with L2 evict-last
-// priority) and scan items S, S(c) interleaved with R(c + lag); the chunk
-// scanner warp turns a chunk's tile counts into tile offsets and chains the
-// chunk prefixes.  An S item loads the tile's payload and flags (the flags again,
+// partitioned one (Section 2.2): a work list of reduce items R and scan items
+// S, S(c) interleaved with R(c + lag); the chunk scanner warp turns a chunk's
+// tile counts into tile offsets and chains the chunk prefixes.  An R item
+// counts the kept elements of kCpGroup consecutive tiles from their flags alone
+// (read with L2 evict-last priority): the flags of one tile are a fifth of its
+// payload, and a work item costs a pipeline stage whatever its size, so a group
+// of four tiles' flags makes an R item as big as an S item's payload.  An S item loads the tile's payload and flags (the flags again,
 // from L2) with its two prefetched status words, gives each thread's kept
 // elements their positions (block exclusive scan of the thread counts),
 // gathers them into shared memory in order, and writes the tile's run of kept
@@ -20,6 +22,80 @@
 
 namespace gbscan {
 
+constexpr int kCpGroup = 4;  // tiles whose flags one R item counts
+constexpr uint32_t kCpEnd = 2;  // stage phase: no more items
+
+// The work list of the compaction (tiles in chunks of K, a multiple of
+// kCpGroup, so that R groups never straddle chunks; R item q counts tiles
+// [q G, q G + G)):
+//   the R items of chunks 0 .. lag-1, then for each chunk c the slot of its
+//   S items and the R items of chunk c + lag, repeating G S items then one R
+//   item while both last, then the rest.
+struct CpOrder {
+    uint32_t K, lag, C, nlast, RK, pre, F, U;
+};
+
+__device__ __forceinline__ CpOrder make_cp_order(int64_t num_tiles, int64_t K, int64_t lag) {
+    CpOrder o;
+    o.K = static_cast<uint32_t>(K);
+    o.lag = static_cast<uint32_t>(lag);
+    o.C = static_cast<uint32_t>((num_tiles + K - 1) / K);
+    o.nlast = static_cast<uint32_t>(num_tiles - static_cast<int64_t>(o.C - 1) * K);
+    o.RK = o.K / kCpGroup;
+    const uint32_t L = o.lag < o.C ? o.lag : o.C;
+    o.pre = L < o.C ? L * o.RK : (o.C - 1) * o.RK + (o.nlast + kCpGroup - 1) / kCpGroup;
+    o.F = o.C > o.lag + 1 ? o.C - 1 - o.lag : 0;
+    o.U = o.K + o.RK;
+    return o;
+}
+
+// Item w: phase kItemReduce with idx = the R group, or kItemScan with idx = the tile.
+__device__ __forceinline__ void compact_item(uint32_t w, const CpOrder& o, uint32_t& phase,
+                                             int64_t& idx) {
+    constexpr uint32_t G = kCpGroup;
+    if (w < o.pre) {
+        phase = kItemReduce;
+        idx = w;
+        return;
+    }
+    w -= o.pre;
+    if (w < o.F * o.U) {
+        const uint32_t c = w / o.U, p = w - c * o.U, q = p / (G + 1), rr = p - q * (G + 1);
+        if (rr < G) {
+            phase = kItemScan;
+            idx = static_cast<int64_t>(c) * o.K + q * G + rr;
+        } else {
+            phase = kItemReduce;
+            idx = static_cast<int64_t>(c + o.lag) * o.RK + q;
+        }
+        return;
+    }
+    w -= o.F * o.U;
+    for (uint32_t c = o.F; c < o.C; ++c) {
+        const uint32_t nS = c < o.C - 1 ? o.K : o.nlast;
+        const uint32_t cr = c + o.lag;
+        const uint32_t nR = cr < o.C ? (cr < o.C - 1 ? o.RK : (o.nlast + G - 1) / G) : 0;
+        if (w < nS + nR) {
+            const int64_t sbase = static_cast<int64_t>(c) * o.K;
+            const int64_t rbase = static_cast<int64_t>(cr) * o.RK;
+            const uint32_t full = nR < nS / G ? nR : nS / G;
+            if (w < full * (G + 1)) {
+                const uint32_t q = w / (G + 1), rr = w - q * (G + 1);
+                phase = rr < G ? kItemScan : kItemReduce;
+                idx = rr < G ? sbase + q * G + rr : rbase + q;
+                return;
+            }
+            const uint32_t p = w - full * (G + 1), remS = nS - full * G;
+            phase = p < remS ? kItemScan : kItemReduce;
+            idx = p < remS ? sbase + full * G + p : rbase + full + (p - remS);
+            return;
+        }
+        w -= nS + nR;
+    }
+    phase = kItemScan;  // not reached for w below the item count
+    idx = 0;
+}
+
 template <int CWARPS, int STAGES>
 struct CpCtrl {
     uint64_t full[STAGES];
@@ -28,6 +104,7 @@ struct CpCtrl {
     uint32_t phase[STAGES];
     alignas(16) unsigned long long stat[STAGES][6];
     unsigned long long wtot[CWARPS];
+    uint32_t gtot[kCpGroup][CWARPS];  // R item: per tile of the group, the warps' counts
     unsigned long long base;  // S item: the output position of the tile's first kept element
     uint32_t kept;            // S item: the tile's kept count
     uint64_t scan_req;
@@ -82,7 +159,9 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
     Header* hdr = p.hdr;
     const int64_t num_tiles = p.num_tiles;
     const int64_t K = p.chunk_tiles;
-    const int64_t num_items = 2 * num_tiles;
+    const int64_t num_groups = (num_tiles + kCpGroup - 1) / kCpGroup;
+    const int64_t num_items = num_tiles + num_groups;
+    static_assert(kCpGroup * TILE <= TILE_BYTES, "an R group's flags fill the payload area");
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -111,7 +190,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
         const uint8_t* __restrict__ fl = p.flags;
         const uint64_t keep = l2_policy_evict_last();
         const uint64_t drop = l2_policy_evict_first();
-        const PtOrder order = make_order(num_tiles, K, p.chunk_lag);
+        const CpOrder order = make_cp_order(num_tiles, K, p.chunk_lag);
         // claims as in the partitioned scan: two items per atomic, the next
         // claim in flight
         unsigned int cur = 0, nxt = 0;
@@ -135,23 +214,28 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             }
             if (w >= num_items) {
                 if (lane == 0) {
-                    c.tile_id[s] = num_tiles;  // end
+                    c.phase[s] = kCpEnd;
                     mbar_arrive(&c.full[s]);
                 }
                 break;
             }
             uint32_t phase;
-            int64_t t;
-            partitioned_item(static_cast<uint32_t>(w), order, phase, t);
-            const int cnt = count_of(t);
-            // flags move by TMA when the slice is whole and 16-byte aligned;
-            // the payload (scan items only) when `in` is aligned and whole too
-            const bool ffast = cnt == TILE && (reinterpret_cast<uintptr_t>(fl) & 15) == 0;
-            const bool xfast = p.fast && cnt == TILE;
+            int64_t t;  // the tile of an S item, the group of an R item
+            compact_item(static_cast<uint32_t>(w), order, phase, t);
+            // an R item's flags (kCpGroup tiles) go to the payload area, an S
+            // item's flags to the flag area; flags move by TMA when the slice
+            // is whole and 16-byte aligned, the payload when `in` is aligned and
+            // the tile whole
+            const int64_t f0 = phase == kItemReduce ? t * kCpGroup * TILE : t * TILE;
+            const int64_t fcap = phase == kItemReduce ? static_cast<int64_t>(kCpGroup) * TILE : TILE;
+            const int fcnt = static_cast<int>((p.n - f0) < fcap ? (p.n - f0) : fcap);
+            const int cnt = phase == kItemScan ? count_of(t) : 0;
+            const bool ffast = fcnt == fcap && (reinterpret_cast<uintptr_t>(fl) & 15) == 0;
+            const bool xfast = p.fast && phase == kItemScan && cnt == TILE;
             T* xb = payload(s);
-            uint8_t* fb = flagbuf(s);
+            uint8_t* fb = phase == kItemReduce ? reinterpret_cast<uint8_t*>(xb) : flagbuf(s);
             if (!ffast) {
-                for (int i = lane; i < cnt; i += 32) fb[i] = fl[t * TILE + i];
+                for (int i = lane; i < fcnt; i += 32) fb[i] = fl[f0 + i];
             }
             if (phase == kItemScan && !xfast) {
                 for (int i = lane; i < cnt; i += 32) xb[i] = in[t * TILE + i];
@@ -161,18 +245,16 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                 c.tile_id[s] = t;
                 c.phase[s] = phase;
                 const uint32_t stat_bytes = phase == kItemScan ? 48u : 0u;
-                const uint32_t tx = (ffast ? static_cast<uint32_t>(TILE) : 0u) +
-                                    (phase == kItemScan && xfast ? static_cast<uint32_t>(TILE_BYTES) : 0u) +
-                                    stat_bytes;
+                const uint32_t tx = (ffast ? static_cast<uint32_t>(fcap) : 0u) +
+                                    (xfast ? static_cast<uint32_t>(TILE_BYTES) : 0u) + stat_bytes;
                 if (tx == 0) {
                     mbar_arrive(&c.full[s]);
                 } else {
                     mbar_arrive_expect_tx(&c.full[s], tx);
                     if (ffast)
-                        bulk_load_hint(fb, fl + t * TILE, TILE, &c.full[s],
+                        bulk_load_hint(fb, fl + f0, static_cast<uint32_t>(fcap), &c.full[s],
                                        phase == kItemReduce ? keep : drop);
-                    if (phase == kItemScan && xfast)
-                        bulk_load_hint(xb, in + t * TILE, TILE_BYTES, &c.full[s], drop);
+                    if (xfast) bulk_load_hint(xb, in + t * TILE, TILE_BYTES, &c.full[s], drop);
                     if (stat_bytes) {
                         bulk_load(&c.stat[s][0], rec_lo(p.rec, t & ~int64_t(1)), 16, &c.full[s]);
                         const uint32_t ch = static_cast<uint32_t>(t) / order.K;
@@ -194,38 +276,44 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                 c.cflag = mbar_wait_bounded(&c.full[s], use & 1u, role_limit, hdr, epoch, true) ? 1u : 0u;
             named_barrier_sync<CTHREADS>(1);
             if (!c.cflag) break;
-            const int64_t t = c.tile_id[s];
-            if (t >= num_tiles) break;
             const uint32_t phase = c.phase[s];
-            const int cnt = count_of(t);
-            uint32_t m = keep_mask<ITEMS>(flagbuf(s) + tid * ITEMS);
-            if (cnt < TILE) m &= valid_items<ITEMS>(cnt, tid);
-            const uint32_t mine = __popc(m);
-            // block exclusive scan of the thread counts
-            uint32_t inc = mine;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
-                if (lane >= d) inc += o;
-            }
-            if (lane == 31) c.wtot[warp] = inc;
-            T x[ITEMS];
-            if (phase == kItemScan) {
-                const T* xb = payload(s);
-#pragma unroll
-                for (int j = 0; j < ITEMS; ++j) x[j] = xb[tid * ITEMS + j];
-            }
-            named_barrier_sync<CTHREADS>(1);  // warp totals written, payload read
+            if (phase == kCpEnd) break;
+            const int64_t t = c.tile_id[s];
             if (phase == kItemReduce) {
+                // ---- R item: the kept counts of the group's tiles ------------
+                const uint8_t* fb = reinterpret_cast<const uint8_t*>(payload(s));
+#pragma unroll
+                for (int g = 0; g < kCpGroup; ++g) {
+                    const int64_t tg = t * kCpGroup + g;
+                    const int cg = tg < num_tiles ? count_of(tg) : 0;
+                    uint32_t mg = 0;
+                    if (cg > 0) {
+                        mg = keep_mask<ITEMS>(fb + g * TILE + tid * ITEMS);
+                        if (cg < TILE) mg &= valid_items<ITEMS>(cg, tid);
+                    }
+                    uint32_t v = __popc(mg);
+#pragma unroll
+                    for (int d = 16; d >= 1; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+                    if (lane == 0) c.gtot[g][warp] = v;
+                }
+                named_barrier_sync<CTHREADS>(1);  // group counts written, flags read
                 if (tid == 0) {
-                    unsigned long long total = 0;
-                    for (int w = 0; w < CWARPS; ++w) total += c.wtot[w];
-                    publish_sum_hooked<Op>(p.rec, t, epoch, cfg, false, total);
+                    for (int g = 0; g < kCpGroup; ++g) {
+                        const int64_t tg = t * kCpGroup + g;
+                        if (tg >= num_tiles) break;
+                        unsigned long long total = 0;
+                        for (int w = 0; w < CWARPS; ++w) total += c.gtot[g][w];
+                        publish_sum_hooked<Op>(p.rec, tg, epoch, cfg, false, total);
+                    }
                     mbar_arrive(&c.empty[s]);
-                    const int64_t ch = static_cast<uint32_t>(t) / static_cast<uint32_t>(K);
+                    // the group holding its chunk's last tile hands the chunk to
+                    // the scanner warp
+                    const int64_t g0 = t * kCpGroup;
+                    const int64_t ch = static_cast<uint32_t>(g0) / static_cast<uint32_t>(K);
                     const int64_t first = ch * K;
                     const int64_t nch = (num_tiles - first) < K ? (num_tiles - first) : K;
-                    if (t == first + nch - 1) {
+                    const int64_t last = first + nch - 1;
+                    if (last >= g0 && last < g0 + kCpGroup) {
                         if (scan_uses > 0 &&
                             !mbar_wait_bounded(&c.scan_idle, (scan_uses - 1) & 1u, role_limit, hdr, epoch,
                                                true))
@@ -239,6 +327,21 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                 }
                 continue;
             }
+            const int cnt = count_of(t);
+            uint32_t m = keep_mask<ITEMS>(flagbuf(s) + tid * ITEMS);
+            if (cnt < TILE) m &= valid_items<ITEMS>(cnt, tid);
+            const uint32_t mine = __popc(m);
+            // block exclusive scan of the thread counts
+            uint32_t inc = mine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += o;
+            }
+            if (lane == 31) c.wtot[warp] = inc;
+            T x[ITEMS];
+            load_items<T, ITEMS, TILE, false>(payload(s), tid, x);
+            named_barrier_sync<CTHREADS>(1);  // warp totals written, payload read
             // ---- scan item: positions of the kept elements, gather, write --
             if (tid == 0) {
                 const int64_t ch = static_cast<uint32_t>(t) / static_cast<uint32_t>(K);
