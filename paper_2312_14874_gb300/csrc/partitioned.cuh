@@ -114,10 +114,9 @@ struct PtCtrl {
     // segmented scans: per stage, the tile's slice of the head bitmap (bit i =
     // element i starts a segment), then zero words for the reads past its end
     alignas(16) uint32_t bits[HEADS != kNoHeads ? STAGES : 1][HEADS != kNoHeads ? TILE / 32 + 4 : 4];
-    Acc wtot_v[CWARPS];
-    uint32_t wtot_f[CWARPS];
+    alignas(16) Acc wtot_v[CWARPS];
+    alignas(16) uint32_t wtot_f[CWARPS];
     Acc prefix_v;
-    uint32_t prefix_f;
     uint64_t scan_req;   // consumers -> scanner warp: a chunk to scan (or -1: stop)
     uint64_t scan_idle;  // scanner warp -> consumers: the request is done
     int64_t scan_chunk;
@@ -514,17 +513,25 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 }
                 named_barrier_sync<CTHREADS>(1);
                 if (tid == 0) {
+                    Acc wt[CWARPS];
+                    uint32_t wtf[CWARPS];
+#pragma unroll
+                    for (int w = 0; w < CWARPS; ++w) {
+                        wt[w] = c.wtot_v[w];
+                        if constexpr (HEADS != kNoHeads) wtf[w] = c.wtot_f[w];
+                    }
                     Acc total = Op::identity();
                     bool total_f = false;
+#pragma unroll
                     for (int w = 0; w < CWARPS; ++w) {
                         if constexpr (HEADS != kNoHeads) {
-                            bool f2 = c.wtot_f[w] != 0;
-                            Acc v2 = c.wtot_v[w];
+                            bool f2 = wtf[w] != 0u;
+                            Acc v2 = wt[w];
                             seg_combine<Op>(total_f, total, f2, v2);
                             total_f = f2;
                             total = v2;
                         } else {
-                            total = Op::combine(total, c.wtot_v[w]);
+                            total = Op::combine(total, wt[w]);
                         }
                     }
                     publish_sum_hooked<Op>(p.rec, t, epoch, cfg, total_f, total);
@@ -578,7 +585,6 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 if constexpr (HEADS != kNoHeads) {
                     seg_combine<Op>(ef, e, of, off);
                     c.prefix_v = off;
-                    c.prefix_f = of ? 1u : 0u;
                 } else {
                     c.prefix_v = Op::combine(e, off);
                 }
@@ -586,6 +592,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             bool wf = tf;
             Acc wv = tv;
             warp_inclusive_scan_w<Op, HEADS>(wh, wf, wv, lane);
+            // xf: a head among the lanes before this one
             bool xf = false;
             if constexpr (HEADS != kNoHeads) xf = __shfl_up_sync(0xffffffffu, wf ? 1 : 0, 1) != 0;
             Acc ev = shfl_up_acc<Op>(wv, 1);
@@ -599,22 +606,31 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             }
             named_barrier_sync<CTHREADS>(1);
             // everything before this thread's first item: the tile's carry, the
-            // warps before this one, the lanes before this one
-            Acc gv = c.prefix_v;
-            if constexpr (HEADS != kNoHeads) {
-                bool gf = c.prefix_f != 0;
-                for (int w = 0; w < warp; ++w) {
-                    bool f2 = c.wtot_f[w] != 0;
-                    Acc v2 = c.wtot_v[w];
-                    seg_combine<Op>(gf, gv, f2, v2);
-                    gf = f2;
-                    gv = v2;
-                }
-                seg_combine<Op>(gf, gv, xf, ev);
-            } else {
-                for (int w = 0; w < warp; ++w) gv = Op::combine(gv, c.wtot_v[w]);
-                ev = Op::combine(gv, ev);
+            // warps before this one, the lanes before this one (a head cuts
+            // what comes before it).  Every warp total is read, with 16-byte
+            // loads, and the loop over them is unrolled: a loop bounded by the
+            // warp index issued one dependent load per warp, on the path that
+            // every scan item waits for.
+            Acc wt[CWARPS];
+            uint32_t wtf[CWARPS];
+#pragma unroll
+            for (int w = 0; w < CWARPS; ++w) {
+                wt[w] = c.wtot_v[w];
+                if constexpr (HEADS != kNoHeads) wtf[w] = c.wtot_f[w];
             }
+            Acc gv = c.prefix_v;
+#pragma unroll
+            for (int w = 0; w < CWARPS; ++w) {
+                if (w < warp) {
+                    if constexpr (HEADS != kNoHeads) {
+                        if (wtf[w] != 0u) gv = wt[w];
+                        else gv = Op::combine(gv, wt[w]);
+                    } else {
+                        gv = Op::combine(gv, wt[w]);
+                    }
+                }
+            }
+            if (!xf) ev = Op::combine(gv, ev);
             T y[ITEMS];
             thread_outputs_w<Op, ITEMS, HEADS>(x, hm, wh, ev, excl, y);
             store_items<T, ITEMS, TILE, false>(buf, tid, y);
