@@ -496,7 +496,7 @@ def main(argv=None) -> int:
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "dtype": "int32", "values": "uniform [0,255]",
                        "algo": algo, "variant": variant, **vinfo,
-                       "l2": "inputs and outputs 4 GiB each, larger than the 129 MB L2: no flush",
+                       "l2": f"input and output {4 * N / 2**30:g} GiB each, larger than the 129 MB L2: no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
