@@ -208,12 +208,13 @@ def inclusive_host(h_in: torch.Tensor, h_out: torch.Tensor | None = None, *,
 
 
 def compact(x: torch.Tensor, flags: torch.Tensor, *, out: torch.Tensor | None = None,
-            variant: int = 0, workspace: Workspace | None = None):
+            variant: int | None = None, workspace: Workspace | None = None):
     """Stream compaction: the elements of ``x`` (int32 or float32, flattened)
     whose ``flags`` (uint8 or bool, same length) are nonzero, in order.  One
     launch (the scan of the flags fused with the gather).  Returns ``(out,
     count)``: ``out`` holds x.numel() elements of which the first ``count``
-    (a 0-d int64 CUDA tensor, read it with ``.item()``) are the result."""
+    (a 0-d int64 CUDA tensor, read it with ``.item()``) are the result.
+    ``variant`` None takes the tuned launch shape for the size."""
     _check_cuda(x, "x")
     _check_cuda(flags, "flags")
     if x.dtype not in (torch.int32, torch.float32):
@@ -230,6 +231,7 @@ def compact(x: torch.Tensor, flags: torch.Tensor, *, out: torch.Tensor | None = 
         if out.dtype != x.dtype or out.numel() < n or out.device != x.device:
             raise ValueError("out must match x in dtype and device and hold x.numel() elements")
     count = torch.empty((), dtype=torch.int64, device=x.device)
+    variant = _variant("compact_" + _DTYPES[x.dtype][1], _DTYPES[x.dtype][1], n, variant)
     ws = workspace or _workspace_for(x.device, workspace_bytes(x.dtype, _capi.KIND_COMPACT, n))
     fn = _capi.lib().compact_i32 if x.dtype == torch.int32 else _capi.lib().compact_f32
     _capi.check(fn(x.data_ptr(), flags.data_ptr(), out.data_ptr(), n, count.data_ptr(), ws.ptr,

@@ -132,10 +132,12 @@ def tune(sizes_log2=(20, 22, 24, 26, 28, 30), write: bool = True, families=None,
                                                                 variant=v)),
     }
     segmented = {"seg_i32": torch.int32, "seg_f32": torch.float32}
+    compaction = {"compact_i32": torch.int32, "compact_f32": torch.float32}
     if families:
         plain = {k: v for k, v in plain.items() if k in families}
         rowwise = {k: v for k, v in rowwise.items() if k in families}
         segmented = {k: v for k, v in segmented.items() if k in families}
+        compaction = {k: v for k, v in compaction.items() if k in families}
     key = gpu_key(dev)
     result: dict = {}
 
@@ -206,6 +208,26 @@ def tune(sizes_log2=(20, 22, 24, 26, 28, 30), write: bool = True, families=None,
                       ", ".join(f"v{v}={t * 1e3:.1f}us" for v, t in enumerate(times)) +
                       f" -> v{best}", flush=True)
             del x, y, o
+    for fam, dtype in compaction.items():
+        # half the elements kept, at random
+        result[fam] = {}
+        nv = gb.num_variants(dtype, _capi.KIND_COMPACT)
+        for lg in sizes(dtype):
+            if lg < 20:
+                continue
+            x = torch.zeros(1 << lg, dtype=dtype, device=dev)
+            y = torch.empty_like(x)
+            g = torch.Generator(device=dev)
+            g.manual_seed(0)
+            f = (torch.rand(1 << lg, device=dev, generator=g) < 0.5).to(torch.uint8)
+            times = [_time_ms(lambda: gb.compact(x, f, out=y, variant=v)) for v in range(nv)]
+            best = min(range(nv), key=lambda v: times[v])
+            result[fam][str(lg)] = best
+            if verbose:
+                print(f"[tune] {fam} n=2^{lg}: " +
+                      ", ".join(f"v{v}={t * 1e3:.1f}us" for v, t in enumerate(times)) +
+                      f" -> v{best}", flush=True)
+            del x, y, f
     if write:
         os.makedirs(TUNED_DIR, exist_ok=True)
         path = table_path(key)
