@@ -452,14 +452,26 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
         T* out = static_cast<T*>(p.out);
         const bool excl = p.exclusive != 0;
         const uint64_t drop = l2_policy_evict_first();
-        int pending = -1;
-        uint32_t scan_uses = 0;  // thread 0: requests sent to the scanner warp
+        // The segmented kernel spreads its serial duties over lanes of three
+        // warps, so that they overlap instead of adding up on the path every
+        // item waits for: thread 0 waits for the stages and reads a scan
+        // item's prefixes, kPubTid publishes tile sums and hands chunks to the
+        // scanner warp, kStoreTid issues the bulk stores and releases their
+        // stages (measured: +2-3% segmented).  The plain kernel keeps them all
+        // on thread 0, with the store's stage released before the next stage
+        // wait (measured: 1-1.5% faster there).
+        constexpr bool kSpread = HEADS != kNoHeads;
+        constexpr int kPubTid = kSpread ? 32 : 0;
+        constexpr int kStoreTid = kSpread ? 64 : 0;
+        static_assert(!kSpread || CWARPS >= 3, "the serial duties take lanes of three warps");
+        int pending = -1;        // kStoreTid: the stage of its last bulk store
+        uint32_t scan_uses = 0;  // kPubTid: requests sent to the scanner warp
         bool scan_ok = true;
         for (uint32_t k = 0;; ++k) {
             const int s = static_cast<int>(k % STAGES);
             const uint32_t use = k / STAGES;
             if (tid == 0) {
-                if (pending >= 0) {
+                if (!kSpread && pending >= 0) {
                     bulk_wait_read_all();
                     mbar_arrive(&c.empty[pending]);
                     pending = -1;
@@ -467,6 +479,12 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 c.cflag = mbar_wait_bounded(&c.full[s], use & 1u, role_limit, hdr, epoch, true) ? 1u : 0u;
             }
             named_barrier_sync<CTHREADS>(1);
+            if (kSpread && tid == kStoreTid && pending >= 0) {
+                // the previous item's store has read its stage by now, mostly
+                bulk_wait_read_all();
+                mbar_arrive(&c.empty[pending]);
+                pending = -1;
+            }
             if (!c.cflag) break;
             const int64_t t = c.tile_id[s];
             if (t >= num_tiles) break;
@@ -512,7 +530,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     if (lane == 0) c.wtot_v[warp] = wv;
                 }
                 named_barrier_sync<CTHREADS>(1);
-                if (tid == 0) {
+                if (tid == kPubTid) {
                     Acc wt[CWARPS];
                     uint32_t wtf[CWARPS];
 #pragma unroll
@@ -536,8 +554,6 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     }
                     publish_sum_hooked<Op>(p.rec, t, epoch, cfg, total_f, total);
                     mbar_arrive(&c.empty[s]);  // every thread holds its items: stage free
-                }
-                if (tid == 0) {
                     const int64_t ch = static_cast<uint32_t>(t) / static_cast<uint32_t>(K);
                     const int64_t first = ch * K;
                     const int64_t nch = (num_tiles - first) < K ? (num_tiles - first) : K;
@@ -637,7 +653,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             if (tile_fast) fence_proxy_async_smem();
             named_barrier_sync<CTHREADS>(1);
             if (tile_fast) {
-                if (tid == 0) {
+                if (tid == kStoreTid) {
                     bulk_store_hint(out + t * TILE, buf, TILE_BYTES, drop);
                     bulk_commit();
                     pending = s;
@@ -648,11 +664,11 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 if (tid == 0) mbar_arrive(&c.empty[s]);
             }
         }
-        if (tid == 0 && pending >= 0) {
-            bulk_wait_read_all();
-            mbar_arrive(&c.empty[pending]);
+        if (tid == kStoreTid) {
+            bulk_wait_all();
+            if (pending >= 0) mbar_arrive(&c.empty[pending]);
         }
-        if (tid == 0) {
+        if (tid == kPubTid) {
             // stop the scanner warp once its last request is done
             if (scan_uses > 0 && scan_ok)
                 scan_ok = mbar_wait_bounded(&c.scan_idle, (scan_uses - 1) & 1u, role_limit, hdr, epoch, true);
