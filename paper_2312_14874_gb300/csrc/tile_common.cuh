@@ -99,16 +99,27 @@ __device__ __forceinline__ void thread_reduce(const typename Op::T (&x)[ITEMS], 
 
 // Inclusive Hillis-Steele scan over the 32 lanes (log2(32) = 5 shift-and-add
 // steps, the in-register scan of Section 3.1 with lanes for SIMD slots).
+// Segmented: one ballot of the head flags gives each lane the last lane at or
+// before it that holds a head (`start`, 0 if none), and a step adds lane
+// lane-d only when lane-d >= start.  That is the condition under which the
+// flag-carrying form (shuffle the flag with the value, add while no head has
+// been seen) adds, so the results are the same, without five flag shuffles.
 template <class Op, int HEADS>
 __device__ __forceinline__ void warp_inclusive_scan(bool& f, typename Op::Acc& v, int lane) {
     using Acc = typename Op::Acc;
+    if constexpr (HEADS != kNoHeads) {
+        const uint32_t upto = __ballot_sync(0xffffffffu, f) & (0xffffffffu >> (31 - lane));
+        const int start = upto ? 31 - __clz(upto) : 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const Acc vo = shfl_up_acc<Op>(v, d);
-        if constexpr (HEADS != kNoHeads) {
-            const bool fo = __shfl_up_sync(0xffffffffu, f ? 1 : 0, d) != 0;
-            if (lane >= d) seg_combine<Op>(fo, vo, f, v);
-        } else {
+        for (int d = 1; d < 32; d <<= 1) {
+            const Acc vo = shfl_up_acc<Op>(v, d);
+            if (lane - d >= start) v = Op::combine(vo, v);
+        }
+        f = upto != 0u;
+    } else {
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const Acc vo = shfl_up_acc<Op>(v, d);
             if (lane >= d) v = Op::combine(vo, v);
         }
     }
