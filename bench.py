@@ -338,9 +338,17 @@ def side_measurements(dev, peak) -> dict:
             g.x.random_(0, 4)
         else:
             g.x.uniform_()
-        rec(f"seg_{'i32' if dt == torch.int32 else 'f32'}_65536segs_exclusive_graph",
+        key = 'i32' if dt == torch.int32 else 'f32'
+        rec(f"seg_{key}_65536segs_exclusive_graph",
             8 * ns + 8 * (off.size), cuda_time_ms(g.replay, reps)[0])
-        del g
+        # the plain scan of the same elements (tuned algorithm), and how much
+        # longer the segmented scan takes per byte
+        yp = torch.empty_like(g.x)
+        rec(f"plain_{key}_same_n_exclusive", 8 * ns, cuda_time_ms(
+            lambda: gb.exclusive(g.x, out=yp, workspace=ws), reps)[0])
+        res[f"seg_{key}_time_per_byte_vs_plain"] = round(
+            res[f"plain_{key}_same_n_exclusive"]["gbs"] / res[f"seg_{key}_65536segs_exclusive_graph"]["gbs"], 3)
+        del g, yp
     res["seg_total_n"] = ns
     # rows [4096, 8192] fp32: forward and backward, L2 flushed between reps
     rows, cols = 4096, 8192
