@@ -316,6 +316,17 @@ def side_measurements(dev, peak) -> dict:
         rec(f"i64_2^29_{algo}", 16 * n64, cuda_time_ms(
             lambda: gb.inclusive(x, out=y, workspace=ws, algo=algo, variant=v), reps)[0])
     del x, y
+    # int32 2^20, U{0..15} (the small configuration: L2-sized, so the L2 is
+    # flushed between reps and the time is reported in microseconds too)
+    n1 = 1 << 20
+    x1 = torch.randint(0, 16, (n1,), dtype=torch.int32, device=dev)
+    y1 = torch.empty_like(x1)
+    flush_small = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ms1 = cuda_time_ms(lambda: gb.inclusive(x1, out=y1, workspace=ws), reps,
+                       lambda: flush_small.fill_(1))[0]
+    rec("i32_2^20_flushed", 8 * n1, ms1)
+    res["i32_2^20_flushed"]["us"] = round(ms1 * 1e3, 2)
+    del x1, y1, flush_small
     # fp32 2^28, plain and compensated
     nf = 1 << 28
     x = torch.randn(nf, device=dev)
@@ -328,6 +339,25 @@ def side_measurements(dev, peak) -> dict:
         rec(f"f32_2^28_compensated_{algo}", 8 * nf, cuda_time_ms(
             lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True, algo=algo, variant=v),
             reps)[0])
+    # fp32 max relative error of the tuned plain and compensated scans:
+    # max_k |y_k - ref_k| / sum_{i<=k} |a_i|, ref = a float64 cumsum on the GPU
+    # (its own error, about log2(n) * 2^-53 relative, is far below what is
+    # measured); on U[0,1) of the 2^-24 grid and on N(0,1)
+    errs = {}
+    for dist, make in (("uniform", lambda: torch.randint(0, 1 << 24, (nf,), device=dev).float() * 2.0 ** -24),
+                       ("normal", lambda: torch.randn(nf, device=dev))):
+        x.copy_(make())
+        ref = torch.cumsum(x.double(), 0)
+        den = torch.cumsum(x.abs().double(), 0)
+        for comp in (False, True):
+            gb.inclusive(x, out=y, workspace=ws, compensated=comp)
+            diff = (y.double() - ref).abs_()
+            rel = torch.where(den > 0, diff / den.clamp_min(1e-300),
+                              torch.where(diff == 0, torch.zeros_like(diff), torch.full_like(diff, float("inf"))))
+            errs[f"{dist}_{'compensated' if comp else 'plain'}"] = float(rel.max().item())
+            del diff, rel
+        del ref, den
+    res["fp32_max_rel_err"] = {"n": nf, "bounds": {"plain": 1e-5, "compensated": 1e-6}, **errs}
     del x, y
     # segmented: 65,536 log-uniform segments in [1, 2^16], exclusive, CUDA graph
     off = synth.segment_offsets(65536, max_log2=16, seed=0)
@@ -518,8 +548,14 @@ def main(argv=None) -> int:
                        "reasons": clk["reasons"], "samples": clk["samples"],
                        "power_w_max": clk.get("power_w_max")},
             "cpu_baseline": cpu,
+            "elements_per_s": round(value * 1e9 / 8, 1),
             "side": side,
         }
+        if side is not None:
+            # the other parts of the metric: % of a device copy of the same
+            # bytes measured in this run, and the fp32 errors
+            line["frac_of_copy_today"] = round(value / side["copy_torch_4GiB"]["gbs"], 4)
+            line["fp32_max_rel_err"] = side["fp32_max_rel_err"]
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
