@@ -562,15 +562,28 @@ def main(argv=None) -> int:
     return 0
 
 
+# The sources the timed int32 partitioned kernel is built and launched from:
+# its template and the tile code it uses, the shared device definitions, the
+# launcher, the int32 variant table, the host dispatch and the C header.  The
+# other kernels' sources (single-pass, two-pass, row-block, compaction) do not
+# change its code.
+STAMP_SOURCES = ("include/gbscan.h",
+                 "paper_2312_14874_gb300/csrc/gbscan_device.cuh",
+                 "paper_2312_14874_gb300/csrc/tile_common.cuh",
+                 "paper_2312_14874_gb300/csrc/partitioned.cuh",
+                 "paper_2312_14874_gb300/csrc/gbscan_launch.cuh",
+                 "paper_2312_14874_gb300/csrc/k_i32.cu",
+                 "paper_2312_14874_gb300/csrc/capi.cu")
+
+
 def _source_stamp() -> str:
-    """Hash of the kernel sources, to tell whether a recorded ncu traffic
-    figure still describes the current kernel."""
+    """Hash of the timed kernel's sources, to tell whether a recorded ncu
+    traffic figure still describes the current kernel."""
     import hashlib
-    import glob
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2312_14874_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(f.read())
+    for rel in STAMP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(rel.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
