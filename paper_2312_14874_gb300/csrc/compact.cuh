@@ -272,8 +272,36 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
         for (uint32_t k = 0;; ++k) {
             const int s = static_cast<int>(k % STAGES);
             const uint32_t use = k / STAGES;
-            if (tid == 0)
+            if (tid == 0) {
                 c.cflag = mbar_wait_bounded(&c.full[s], use & 1u, role_limit, hdr, epoch, true) ? 1u : 0u;
+                if (c.cflag && c.phase[s] == kItemScan) {
+                    // the output position of the tile's run: the chunk prefix
+                    // plus the tile's offset within the chunk, from the
+                    // prefetched copies (the words themselves only if a copy was
+                    // taken before its word was published)
+                    const int64_t ts = c.tile_id[s];
+                    const int64_t ch = static_cast<uint32_t>(ts) / static_cast<uint32_t>(K);
+                    unsigned long long e, off;
+                    uint32_t se, so;
+                    bool hf;
+                    parse_words<Op>(c.stat[s][4], c.stat[s][5], epoch, se, hf, e);
+                    parse_words<Op>(c.stat[s][ts & 1], c.stat[s][2 + (ts & 1)], epoch, so, hf, off);
+                    const uint64_t t0 = global_timer_ns();
+                    while (se != kStateP || so != kStateP) {
+                        if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
+                            record_timeout(hdr, epoch, ts);
+                            break;
+                        }
+                        __nanosleep(64);
+                        poll_round_fence();
+                        if (se != kStateP)
+                            read_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, se, hf, e);
+                        if (so != kStateP)
+                            read_words<Op>(rec_lo(p.rec, ts), rec_hi(p.rec, ts), epoch, so, hf, off);
+                    }
+                    c.base = e + off;
+                }
+            }
             named_barrier_sync<CTHREADS>(1);
             if (!c.cflag) break;
             const uint32_t phase = c.phase[s];
@@ -344,41 +372,27 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             named_barrier_sync<CTHREADS>(1);  // warp totals written, payload read
             // ---- scan item: positions of the kept elements, gather, write --
             if (tid == 0) {
-                const int64_t ch = static_cast<uint32_t>(t) / static_cast<uint32_t>(K);
-                unsigned long long e, off;
-                uint32_t se, so;
-                bool hf;
-                parse_words<Op>(c.stat[s][4], c.stat[s][5], epoch, se, hf, e);
-                parse_words<Op>(c.stat[s][t & 1], c.stat[s][2 + (t & 1)], epoch, so, hf, off);
-                const uint64_t t0 = global_timer_ns();
-                while (se != kStateP || so != kStateP) {
-                    if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
-                        record_timeout(hdr, epoch, t);
-                        break;
-                    }
-                    __nanosleep(64);
-                    poll_round_fence();
-                    if (se != kStateP)
-                        read_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, se, hf, e);
-                    if (so != kStateP)
-                        read_words<Op>(rec_lo(p.rec, t), rec_hi(p.rec, t), epoch, so, hf, off);
-                }
-                c.base = e + off;
                 uint32_t total = 0;
                 for (int w = 0; w < CWARPS; ++w) total += static_cast<uint32_t>(c.wtot[w]);
                 c.kept = total;
             }
-            uint32_t pos = inc - mine;  // this thread's first position in the tile's run
+            // The run is gathered at stage index shift + (position in the run),
+            // shift = base mod 4, so that stage index i and output element
+            // base - shift + i share their 16-byte alignment; the up to three
+            // elements past the payload area land in the flag area, whose flags
+            // every thread has read.
+            const unsigned long long base = c.base;
+            const uint32_t shift = static_cast<uint32_t>(base & 3ull);
+            uint32_t pos = shift + inc - mine;  // this thread's first stage index
             for (int w = 0; w < warp; ++w) pos += static_cast<uint32_t>(c.wtot[w]);
             T* xb = payload(s);
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)
                 if ((m >> j) & 1u) {
-                    if (pos < static_cast<uint32_t>(TILE)) xb[pos] = x[j];
+                    if (pos < static_cast<uint32_t>(TILE) + 3u) xb[pos] = x[j];
                     ++pos;
                 }
-            named_barrier_sync<CTHREADS>(1);  // the run is gathered; base and kept are set
-            const unsigned long long base = c.base;
+            named_barrier_sync<CTHREADS>(1);  // the run is gathered; kept is set
             uint32_t kept = c.kept;
             // a run that would leave the output (only after a failed wait, which
             // has recorded its error) is not written
@@ -387,7 +401,23 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                 if (tid == 0) record_error(hdr, GBSCAN_ERR_INVALID_ARG, t);
                 kept = 0;
             }
-            for (uint32_t i = tid; i < kept; i += CTHREADS) out[base + i] = xb[i];
+            const uint32_t span = shift + kept;  // stage indices [shift, span) hold the run
+            T* og = out + (base - shift);        // output element of stage index 0
+            if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+                // 16-byte stores for the whole groups of four, single elements
+                // at the two ends of the run
+                for (uint32_t i0 = 4u * tid; i0 < span; i0 += 4u * CTHREADS) {
+                    if (i0 >= shift && i0 + 4u <= span) {
+                        *reinterpret_cast<uint4*>(og + i0) = *reinterpret_cast<const uint4*>(xb + i0);
+                    } else {
+#pragma unroll
+                        for (uint32_t q = 0; q < 4u; ++q)
+                            if (i0 + q >= shift && i0 + q < span) og[i0 + q] = xb[i0 + q];
+                    }
+                }
+            } else {
+                for (uint32_t i = shift + tid; i < span; i += CTHREADS) og[i] = xb[i];
+            }
             named_barrier_sync<CTHREADS>(1);  // the stage is read
             if (tid == 0) mbar_arrive(&c.empty[s]);
         }
