@@ -96,6 +96,40 @@ def barrier(device=None):
 
 # ---- clocks ------------------------------------------------------------------
 
+def bind_to_gpu_cpus(gpu_index: int):
+    """Binds the calling thread to the CPUs that NVML lists as local to the GPU,
+    so that the pinned host buffers allocated next sit in the GPU's NUMA node
+    (on a two-socket host, pages on the far socket cross one more link on
+    every copy).  Read-only NVML queries; nothing about the GPU changes.
+    Returns the CPUs, or None where NVML or the query is unavailable."""
+    import ctypes
+    try:
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+    except OSError:
+        return None
+    if nv.nvmlInit_v2() != 0:
+        return None
+    try:
+        h = ctypes.c_void_p()
+        if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(h)) != 0:
+            return None
+        words = ((os.cpu_count() or 64) + 63) // 64
+        mask = (ctypes.c_ulong * words)()
+        if nv.nvmlDeviceGetCpuAffinity(h, ctypes.c_uint(words), mask) != 0:
+            return None
+        allowed = os.sched_getaffinity(0)
+        cpus = [64 * i + b for i in range(words) for b in range(64)
+                if (mask[i] >> b) & 1 and 64 * i + b in allowed]
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return cpus
+    except (OSError, AttributeError):
+        return None
+    finally:
+        nv.nvmlShutdown()
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 100 ms while active."""
 
@@ -424,6 +458,7 @@ def main(argv=None) -> int:
     peak, peak_kind = measured_hbm_peak()
 
     # host input in pinned memory (also the source of the e2e copies)
+    local_cpus = bind_to_gpu_cpus(dev.index if dev.index is not None else 0)
     h_in = torch.empty(N, dtype=torch.int32, pin_memory=True)
     synth.uniform_i32_into(h_in.data_ptr(), N, VALUE_RANGE, seed=0)
     x = h_in.to(dev)
@@ -495,7 +530,9 @@ def main(argv=None) -> int:
         e2e_secs = max_over_ranks(a.elapsed_time(b) / 1e3 / e2e_steps, dev)
         e2e = {"value": round(aggregate(BYTES_PER_STEP, e2e_secs, world), 3), "unit": "GB/s",
                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
-               "ms_per_step": round(e2e_secs * 1e3, 3)}
+               "ms_per_step": round(e2e_secs * 1e3, 3),
+               "host_buffers": (f"pinned, allocated from {len(local_cpus)} CPUs local to the GPU (NVML)"
+                                if local_cpus else "pinned")}
         del h_out
 
     cpu = None
