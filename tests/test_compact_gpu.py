@@ -57,6 +57,13 @@ def test_compact_misaligned_and_bool_flags():
     out, cnt = gb.compact(xa[:n], fa[:n] != 0)  # bool flags
     want = oracle.compact(a[:n], f[:n])
     assert int(cnt.item()) == want.size and np.array_equal(out[:want.size].cpu().numpy(), want)
+    # output at an element offset (not 16-byte aligned): the runs leave with
+    # single-element stores; the guard words around it stay untouched
+    ob = torch.full((n + 2,), -7, dtype=torch.int32, device=dev())
+    out, cnt = gb.compact(xa[:n], fa[:n], out=ob[1:n + 1])
+    k = int(cnt.item())
+    assert k == want.size and np.array_equal(out[:k].cpu().numpy(), want)
+    assert int(ob[0].item()) == -7 and int(ob[n + 1].item()) == -7
     assert gb.device_status() == 0
 
 
