@@ -199,6 +199,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             nxt = atomicAdd(&hdr->tile_counter, static_cast<unsigned int>(kClaim));
         }
         int in_batch = 0;
+        uint32_t fills = 0;  // stage fills made, in order (see drain_fills)
         for (uint32_t k = 0;; ++k) {
             const int s = static_cast<int>(k % STAGES);
             const uint32_t use = k / STAGES;
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                     nxt = atomicAdd(&hdr->tile_counter, static_cast<unsigned int>(kClaim));
                 }
             }
+            ++fills;
             if (w >= num_items) {
                 if (lane == 0) {
                     c.phase[s] = kCpEnd;
@@ -234,27 +236,29 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             const bool xfast = p.fast && phase == kItemScan && cnt == TILE;
             T* xb = payload(s);
             uint8_t* fb = phase == kItemReduce ? reinterpret_cast<uint8_t*>(xb) : flagbuf(s);
-            if (!ffast) {
-                for (int i = lane; i < fcnt; i += 32) fb[i] = fl[f0 + i];
-            }
-            if (phase == kItemScan && !xfast) {
-                for (int i = lane; i < cnt; i += 32) xb[i] = in[t * TILE + i];
-            }
+            // ragged or misaligned parts: aligned bodies by bulk copies, the
+            // rest by the lanes
+            uint32_t fbytes = ffast ? static_cast<uint32_t>(fcap) : 0u;
+            uint32_t xbytes = xfast ? static_cast<uint32_t>(TILE_BYTES) : 0u;
+            if (!ffast)
+                fbytes = warp_stage_partial<uint8_t>(fb, fl + f0, fcnt, fcnt,
+                                                     (reinterpret_cast<uintptr_t>(fl) & 15) == 0,
+                                                     uint8_t(0), lane);
+            if (phase == kItemScan && !xfast)
+                xbytes = warp_stage_partial<T>(xb, in + t * TILE, cnt, cnt, p.fast, T(0), lane);
             __syncwarp();
             if (lane == 0) {
                 c.tile_id[s] = t;
                 c.phase[s] = phase;
                 const uint32_t stat_bytes = phase == kItemScan ? 48u : 0u;
-                const uint32_t tx = (ffast ? static_cast<uint32_t>(fcap) : 0u) +
-                                    (xfast ? static_cast<uint32_t>(TILE_BYTES) : 0u) + stat_bytes;
+                const uint32_t tx = fbytes + xbytes + stat_bytes;
                 if (tx == 0) {
                     mbar_arrive(&c.full[s]);
                 } else {
                     mbar_arrive_expect_tx(&c.full[s], tx);
-                    if (ffast)
-                        bulk_load_hint(fb, fl + f0, static_cast<uint32_t>(fcap), &c.full[s],
-                                       phase == kItemReduce ? keep : drop);
-                    if (xfast) bulk_load_hint(xb, in + t * TILE, TILE_BYTES, &c.full[s], drop);
+                    if (fbytes)
+                        bulk_load_hint(fb, fl + f0, fbytes, &c.full[s], phase == kItemReduce ? keep : drop);
+                    if (xbytes) bulk_load_hint(xb, in + t * TILE, xbytes, &c.full[s], drop);
                     if (stat_bytes) {
                         bulk_load(&c.stat[s][0], rec_lo(p.rec, t & ~int64_t(1)), 16, &c.full[s]);
                         const uint32_t ch = static_cast<uint32_t>(t) / order.K;
@@ -264,7 +268,10 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                 }
             }
         }
-        if (lane == 0) *static_cast<volatile unsigned int*>(&c.claim_sink) = cur ^ nxt;
+        if (lane == 0) {
+            *static_cast<volatile unsigned int*>(&c.claim_sink) = cur ^ nxt;
+            drain_fills<STAGES>(c.full, fills, role_limit, hdr);
+        }
     } else if (warp < CWARPS) {
         T* out = static_cast<T*>(p.out);
         uint32_t scan_uses = 0;

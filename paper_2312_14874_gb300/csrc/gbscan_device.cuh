@@ -331,13 +331,21 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
     return v;
 }
 
+// Set in the claim counter by an abort: every later claim of the launch
+// returns at least 2^31, past any tile or item count (all below 2^31), so that
+// no block takes new work.  The last block to finish resets the counter.
+constexpr uint32_t kClaimPoison = 0x80000000u;
+
 // A bounded wait ran out in the launch tagged `epoch`: record the error (kept
-// until scan_get_device_status reads it) and mark the launch aborted, so that
-// its other waits give up at once instead of each running into the bound.
-// The mark names the launch, so later launches are not affected.
+// until scan_get_device_status reads it), mark the launch aborted, so that its
+// other waits give up at once instead of each running into the bound, and
+// poison the claim counter, so that the blocks finish the items they hold and
+// claim no more.  The mark names the launch, so later launches are not
+// affected.
 __device__ __forceinline__ void record_timeout(Header* hdr, uint32_t epoch, int64_t tile) {
     record_error(hdr, GBSCAN_ERR_TIMEOUT, tile);
     atomicExch(&hdr->abort_epoch, epoch);
+    atomicOr(&hdr->tile_counter, kClaimPoison);
 }
 
 __device__ __forceinline__ bool launch_aborted(const Header* hdr, uint32_t epoch) {

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "lookback.cuh"
 #include "partitioned.cuh"
 #include "rows.cuh"
 #include "compact.cuh"
@@ -84,6 +85,13 @@ cudaError_t launch_ws(const Params& p, cudaStream_t stream) {
                              occ_cache, p, stream);
 }
 
+template <class Op, int NW, int NV, int STAGES, int LB, int MINB>
+cudaError_t launch_lb(const Params& p, cudaStream_t stream) {
+    static std::atomic<int> occ_cache[64];
+    return launch_persistent(lb_scan_kernel<Op, NW, NV, STAGES, LB, MINB>, lb_threads<NW, STAGES>(),
+                             lb_smem_bytes<Op, NW, NV, STAGES>(), occ_cache, p, stream);
+}
+
 template <class Op, int THREADS, int ITEMS, int STAGES, int MODE>
 cudaError_t launch_tp(const Params& p, cudaStream_t stream) {
     static std::atomic<int> occ_cache[64];
@@ -156,11 +164,17 @@ cudaError_t launch_scan_sums(unsigned long long* rec, int64_t num_tiles, cudaStr
         (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, kRowHeads, REV_, LB, MB>, \
             nullptr, nullptr, nullptr, 0, &launch_rb<OP, RCW, RI, RS, REV_, RMB>, RCW * 32 * RI   \
     }
-#define GBSCAN_VARIANT_ALL(OP, CW, I, S, LB, MB, TS)                                          \
-    Variant {                                                                                 \
-        (CW + 1 + S) * 32, I, S, CW * 32 * I, &launch_ws<OP, CW, I, S, kNoHeads, false, LB, MB>, \
+// Plain scans: one tile (CW consumer warps x I items) for all three
+// algorithms.  Single-pass: the look-back kernel with SPS stages and SPMB
+// blocks per SM (CW consumer warps, a loader warp and SPS agent warps; the
+// group walk reads one group word per lane and round).  Two-pass: CW * 32
+// threads, TS stages.  Partitioned: PTS stages, PTMB blocks per SM.
+#define GBSCAN_VARIANT_ALL(OP, CW, I, SPS, SPMB, TS, PTS, PTMB)                                  \
+    Variant {                                                                                   \
+        (CW + 1 + SPS) * 32, I, SPS, CW * 32 * I,                                               \
+            &launch_lb<OP, CW, I / (16 / static_cast<int>(sizeof(OP::T))), SPS, 1, SPMB>,        \
             &launch_tp<OP, CW * 32, I, TS, kReduce>, &launch_tp<OP, CW * 32, I, TS, kScanOffset>, \
-            &launch_pt<OP, CW, I, (S > 2 ? S : 3), (MB > 2 ? 2 : MB), kNoHeads>, kMaxChunkTiles      \
+            &launch_pt<OP, CW, I, PTS, PTMB, kNoHeads>, kMaxChunkTiles                           \
     }
 
 // Families, one per translation unit group.

@@ -5,15 +5,16 @@
 namespace gbscan {
 
 static const Variant kScanF32[] = {
-    GBSCAN_VARIANT_ALL(OpF32, 8, 20, 3, 8, 3, 2),
-    GBSCAN_VARIANT_ALL(OpF32, 8, 20, 4, 8, 2, 2),
-    GBSCAN_VARIANT_ALL(OpF32, 8, 12, 4, 8, 3, 3),
-    GBSCAN_VARIANT_ALL(OpF32, 16, 20, 2, 8, 2, 1),
-    GBSCAN_VARIANT_ALL(OpF32, 4, 28, 4, 16, 4, 3),
+    GBSCAN_VARIANT_ALL(OpF32, 8, 20, 3, 3, 2, 3, 2),
+    GBSCAN_VARIANT_ALL(OpF32, 8, 20, 5, 2, 2, 4, 2),
+    GBSCAN_VARIANT_ALL(OpF32, 8, 12, 6, 2, 3, 4, 2),
+    GBSCAN_VARIANT_ALL(OpF32, 16, 20, 5, 1, 1, 3, 2),
+    GBSCAN_VARIANT_ALL(OpF32, 4, 28, 4, 3, 3, 4, 2),
+    GBSCAN_VARIANT_ALL(OpF32, 8, 28, 4, 2, 2, 3, 2),
 };
 
 const Family& family_scan_f32() {
-    static const Family f{5, kScanF32, &launch_scan_sums<OpF32>};
+    static const Family f{6, kScanF32, &launch_scan_sums<OpF32>};
     return f;
 }
 

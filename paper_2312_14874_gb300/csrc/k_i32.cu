@@ -5,15 +5,16 @@
 namespace gbscan {
 
 static const Variant kScanI32[] = {
-    GBSCAN_VARIANT_ALL(OpI32, 8, 20, 3, 8, 3, 2),
-    GBSCAN_VARIANT_ALL(OpI32, 8, 20, 4, 8, 2, 2),
-    GBSCAN_VARIANT_ALL(OpI32, 8, 12, 4, 8, 3, 3),
-    GBSCAN_VARIANT_ALL(OpI32, 16, 20, 2, 8, 2, 1),
-    GBSCAN_VARIANT_ALL(OpI32, 4, 28, 4, 16, 4, 3),
+    GBSCAN_VARIANT_ALL(OpI32, 8, 20, 3, 3, 2, 3, 2),
+    GBSCAN_VARIANT_ALL(OpI32, 8, 20, 5, 2, 2, 4, 2),
+    GBSCAN_VARIANT_ALL(OpI32, 8, 12, 6, 2, 3, 4, 2),
+    GBSCAN_VARIANT_ALL(OpI32, 16, 20, 5, 1, 1, 3, 2),
+    GBSCAN_VARIANT_ALL(OpI32, 4, 28, 4, 3, 3, 4, 2),
+    GBSCAN_VARIANT_ALL(OpI32, 8, 28, 4, 2, 2, 3, 2),
 };
 
 const Family& family_scan_i32() {
-    static const Family f{5, kScanI32, &launch_scan_sums<OpI32>};
+    static const Family f{6, kScanI32, &launch_scan_sums<OpI32>};
     return f;
 }
 

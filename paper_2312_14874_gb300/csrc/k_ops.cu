@@ -1,6 +1,6 @@
 // k_ops.cu — scans under other associative operators than +: running maximum
 // and running minimum of int32 and fp32 arrays (single-pass, two-pass and
-// partitioned, two launch shapes each); and stream compaction, the scan of
+// partitioned, three launch shapes each); and stream compaction, the scan of
 // keep flags fused with the gather it drives.
 #include "gbscan_launch.cuh"
 
@@ -8,11 +8,12 @@ namespace gbscan {
 
 #define GBSCAN_OP_FAMILY(FN, OP)                                                                \
     static const Variant kVariants##OP[] = {                                                    \
-        GBSCAN_VARIANT_ALL(OP, 8, 20, 3, 8, 3, 2),                                              \
-        GBSCAN_VARIANT_ALL(OP, 8, 20, 4, 8, 2, 2),                                              \
+        GBSCAN_VARIANT_ALL(OP, 8, 20, 3, 3, 2, 3, 2),                                           \
+        GBSCAN_VARIANT_ALL(OP, 8, 20, 5, 2, 2, 4, 2),                                           \
+        GBSCAN_VARIANT_ALL(OP, 8, 28, 4, 2, 2, 3, 2),                                           \
     };                                                                                          \
     const Family& FN() {                                                                        \
-        static const Family f{2, kVariants##OP, &launch_scan_sums<OP>};                         \
+        static const Family f{3, kVariants##OP, &launch_scan_sums<OP>};                         \
         return f;                                                                               \
     }
 

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
     if (warp == LOAD_WARP) {
         // ---- a1: claim tiles in order and start their loads --------------------
         const T* __restrict__ in = static_cast<const T*>(p.in);
+        uint32_t fills = 0;  // stage fills made, in order (see drain_fills)
         for (uint32_t k = 0;; ++k) {
             const int s = static_cast<int>(k % STAGES);
             const uint32_t use = k / STAGES;
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
                     mbar_arrive(&c.full[s]);
                     if (HEADS == kOffsetHeads) mbar_arrive(&c.full[s]);
                 }
+                ++fills;
                 for (uint32_t k2 = k + 1; k2 < k + STAGES; ++k2) {
                     const int s2 = static_cast<int>(k2 % STAGES);
                     const uint32_t use2 = k2 / STAGES;
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
                         mbar_arrive(&c.full[s2]);
                         if (HEADS == kOffsetHeads) mbar_arrive(&c.full[s2]);
                     }
+                    ++fills;
                 }
                 break;
             }
@@ -151,12 +154,20 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
                     bulk_load(buf, in + tb, TILE_BYTES, &c.full[s]);
                 }
             } else {
+                // ragged or misaligned: the aligned body by one bulk copy where
+                // the stage offset allows, the rest by the lanes
                 const int off = REVERSE ? TILE - cnt : 0;
-                for (int i = lane; i < cnt; i += 32) buf[off + i] = in[tb + i];
+                const bool bulk_ok = p.fast && ((off * static_cast<int>(sizeof(T))) & 15) == 0;
+                const uint32_t bulk = warp_stage_partial<T>(buf + off, in + tb, cnt, cnt, bulk_ok, Op::pad(), lane);
                 __syncwarp();
                 if (lane == 0) {
                     c.tile_id[s] = tile;
-                    mbar_arrive(&c.full[s]);
+                    if (bulk) {
+                        mbar_arrive_expect_tx(&c.full[s], bulk);
+                        bulk_load(buf + off, in + tb, bulk, &c.full[s]);
+                    } else {
+                        mbar_arrive(&c.full[s]);
+                    }
                 }
             }
             if constexpr (HEADS == kOffsetHeads) {
@@ -169,7 +180,9 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
                     mbar_arrive(&c.full[s]);
                 }
             }
+            ++fills;
         }
+        if (lane == 0) drain_fills<STAGES>(c.full, fills, role_limit, hdr);
     } else if (warp > LOAD_WARP) {
         // ---- a5: stage agent: tile sum as soon as the data lands, look-back --
         const int s = warp - LOAD_WARP - 1;
@@ -397,6 +410,7 @@ struct TpCtrl {
     using Acc = typename Op::Acc;
     uint64_t mbar[STAGES];
     Acc wtot_v[2][NWARPS];
+    uint32_t cflag;  // thread 0 -> block: the stage wait succeeded
 };
 
 template <class Op, int THREADS, int ITEMS, int STAGES>
@@ -420,7 +434,19 @@ __global__ void __launch_bounds__(THREADS) two_pass_kernel(const Params p) {
     const T* __restrict__ in = static_cast<const T*>(p.in);
     T* out = static_cast<T*>(p.out);
     const int64_t num_tiles = p.num_tiles;
-    const uint64_t limit_ns = kDefaultSpinLimitNs;
+    // The blocks of a two-pass launch never wait for one another: the only
+    // waits are a block's own stage loads.  A stage wait that runs out records
+    // GBSCAN_ERR_TIMEOUT and ends the block's loop at once (its remaining
+    // tiles are not computed, and the error tells the host so); the block
+    // then waits, again bounded, for the loads it still has in flight, so a
+    // launch lasts at most its normal time plus two spin limits.  A stage
+    // whose wait failed is never re-armed: arming it again while the late
+    // load's bytes are still owed to the old phase would leave the barrier's
+    // phase and the expected parity out of step, and every later wait of the
+    // block would then run to its bound.
+    const LookbackCfg cfg = read_lookback_cfg(p.hdr);
+    const uint64_t limit_ns = cfg.spin_limit_ns;
+    uint32_t armed = 0;  // thread 0: stages with a load issued and not yet consumed
 
     auto tile_of = [&](uint32_t k) -> int64_t {
         return static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(k) * gridDim.x;
@@ -432,9 +458,11 @@ __global__ void __launch_bounds__(THREADS) two_pass_kernel(const Params p) {
     auto issue = [&](uint32_t k) {
         const int64_t t = tile_of(k);
         if (t < num_tiles && p.fast && count_of(t) == TILE) {
+            if (t == cfg.drop_tile) return;  // test hook: this tile's stage never fills
             const int s = static_cast<int>(k % STAGES);
             mbar_arrive_expect_tx(&c.mbar[s], TILE_BYTES);
             bulk_load(smem + s * TILE_BYTES, in + t * TILE, TILE_BYTES, &c.mbar[s]);
+            armed |= 1u << s;
         }
     };
     if (tid == 0) {
@@ -443,7 +471,7 @@ __global__ void __launch_bounds__(THREADS) two_pass_kernel(const Params p) {
         for (int s = 0; s < STAGES; ++s) issue(static_cast<uint32_t>(s));
     }
     __syncthreads();
-    uint32_t phase = 0;
+    uint32_t phase = 0;  // per stage: the parity of the next phase to wait for
     bool refill_pending = false;
     for (uint32_t k = 0;; ++k) {
         const int64_t tile = tile_of(k);
@@ -454,11 +482,19 @@ __global__ void __launch_bounds__(THREADS) two_pass_kernel(const Params p) {
         T* buf = reinterpret_cast<T*>(smem + s * TILE_BYTES);
         if (tile_fast) {
             // one thread observes the phase; the block barrier passes its view
-            // of the bulk-copied data on to every thread
-            const uint32_t par = (phase >> s) & 1u;
-            phase ^= 1u << s;
-            if (tid == 0) mbar_wait_bounded(&c.mbar[s], par, limit_ns, p.hdr, 0, true);
+            // of the bulk-copied data (and the outcome) on to every thread
+            if (tid == 0) {
+                const bool ok =
+                    mbar_wait_bounded(&c.mbar[s], (phase >> s) & 1u, limit_ns, p.hdr, 0, false);
+                if (ok)
+                    armed &= ~(1u << s);
+                else
+                    record_error(p.hdr, GBSCAN_ERR_TIMEOUT, tile);
+                c.cflag = ok ? 1u : 0u;
+            }
             __syncthreads();
+            if (!c.cflag) break;
+            phase ^= 1u << s;
         } else {
             for (int i = tid; i < cnt; i += THREADS) buf[i] = in[tile * TILE + i];
             __syncthreads();
@@ -528,7 +564,13 @@ __global__ void __launch_bounds__(THREADS) two_pass_kernel(const Params p) {
             }
         }
     }
-    if (tid == 0) bulk_wait_all();
+    if (tid == 0) {
+        // loads still in flight (only after a failed wait) must land before
+        // the block's shared memory is given up
+        for (int s = 0; s < STAGES; ++s)
+            if ((armed >> s) & 1u) mbar_wait_bounded(&c.mbar[s], (phase >> s) & 1u, limit_ns, p.hdr, 0, false);
+        bulk_wait_all();
+    }
 }
 
 // Exclusive scan of the two-pass tile sums (aux fields), one block.

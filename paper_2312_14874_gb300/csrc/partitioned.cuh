@@ -387,6 +387,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             nxt = atomicAdd(&hdr->tile_counter, static_cast<unsigned int>(kClaim));
         }
         int in_batch = 0;
+        uint32_t fills = 0;  // stage fills made, in order (see drain_fills)
         for (uint32_t k = 0;; ++k) {
             const int s = static_cast<int>(k % STAGES);
             const uint32_t use = k / STAGES;
@@ -400,8 +401,10 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     nxt = atomicAdd(&hdr->tile_counter, static_cast<unsigned int>(kClaim));
                 }
             }
+            ++fills;
             if (w >= num_items) {
-                // end: a sentinel stage ends the consumers' loop
+                // end (or an aborted launch: poisoned claims): a sentinel
+                // stage ends the consumers' loop
                 if (lane == 0) {
                     c.tile_id[s] = num_tiles;
                     mbar_arrive(&c.full[s]);
@@ -414,21 +417,24 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             const int cnt = count_of(t);
             const bool fast = p.fast && cnt == TILE;
             T* buf = reinterpret_cast<T*>(smem + s * TILE_BYTES);
+            // a whole aligned tile moves by one bulk copy; a ragged one by a
+            // bulk copy of its aligned body and the lanes for the rest
+            uint32_t body = fast ? static_cast<uint32_t>(TILE_BYTES) : 0u;
             if (!fast) {
-                for (int i = lane; i < cnt; i += 32) buf[i] = in[t * TILE + i];
+                body = warp_stage_partial<T>(buf, in + t * TILE, cnt, cnt, p.fast, Op::pad(), lane);
                 __syncwarp();
             }
             if (lane == 0) {
                 c.tile_id[s] = t;
                 c.phase[s] = phase;
                 const uint32_t stat_bytes = phase == kItemScan ? (Op::kPacked ? 32u : 48u) : 0u;
-                const uint32_t tx = (fast ? TILE_BYTES : 0u) + stat_bytes + BITS_BYTES;
+                const uint32_t tx = body + stat_bytes + BITS_BYTES;
                 if (tx == 0) {
                     mbar_arrive(&c.full[s]);
                 } else {
                     mbar_arrive_expect_tx(&c.full[s], tx);
-                    if (fast)
-                        bulk_load_hint(buf, in + t * TILE, TILE_BYTES, &c.full[s],
+                    if (body)
+                        bulk_load_hint(buf, in + t * TILE, body, &c.full[s],
                                        phase == kItemReduce ? keep : drop);
                     if constexpr (HEADS != kNoHeads)
                         bulk_load(&c.bits[s][0], p.bitmap + t * (TILE / 32), BITS_BYTES, &c.full[s]);
@@ -447,7 +453,10 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
         // the claims still in flight must land before this block reports itself
         // done (the last block to finish resets the counter): the store waits
         // for the atomics' results
-        if (lane == 0) *static_cast<volatile unsigned int*>(&c.claim_sink) = cur ^ nxt;
+        if (lane == 0) {
+            *static_cast<volatile unsigned int*>(&c.claim_sink) = cur ^ nxt;
+            drain_fills<STAGES>(c.full, fills, role_limit, hdr);
+        }
     } else if (warp < CWARPS) {
         T* out = static_cast<T*>(p.out);
         const bool excl = p.exclusive != 0;

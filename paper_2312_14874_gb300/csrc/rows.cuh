@@ -93,11 +93,13 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) rowblock_kernel(const
     if (warp == LOAD_WARP) {
         const T* __restrict__ in = static_cast<const T*>(p.in);
         int64_t i = blockIdx.x;
+        uint32_t fills = 0;  // stage fills made, in order (see drain_fills)
         for (uint32_t u = 0;; ++u, i += gridDim.x) {
             const int s = static_cast<int>(u % STAGES);
             const uint32_t use = u / STAGES;
             if (use > 0 && !warp_wait(&c.empty[s], (use - 1) & 1u, role_limit, hdr, epoch, lane))
                 break;
+            ++fills;
             if (i >= num_items) {
                 if (lane == 0) {
                     c.item[s] = -1;  // end
@@ -108,14 +110,19 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) rowblock_kernel(const
             const int cnt = item_count(i);
             const int64_t tb = i * k * cols;
             T* buf = reinterpret_cast<T*>(smem + s * TILE_BYTES) + (REVERSE ? TILE - cnt : 0);
+            uint32_t bytes = fast ? static_cast<uint32_t>(cnt) * static_cast<uint32_t>(sizeof(T)) : 0u;
             if (!fast) {
-                for (int j = lane; j < cnt; j += 32) buf[j] = in[tb + j];
+                // rows not in whole 16-byte units: the aligned body of the item
+                // by one bulk copy where source and stage allow, the rest by the
+                // lanes
+                const bool bulk_ok = p.fast && ((tb * static_cast<int64_t>(sizeof(T))) & 15) == 0 &&
+                                     (reinterpret_cast<uintptr_t>(buf) & 15) == 0;
+                bytes = warp_stage_partial<T>(buf, in + tb, cnt, cnt, bulk_ok, Op::pad(), lane);
                 __syncwarp();
             }
             if (lane == 0) {
                 c.item[s] = i;
-                if (fast) {
-                    const uint32_t bytes = static_cast<uint32_t>(cnt) * static_cast<uint32_t>(sizeof(T));
+                if (bytes) {
                     mbar_arrive_expect_tx(&c.full[s], bytes);
                     bulk_load(buf, in + tb, bytes, &c.full[s]);
                 } else {
@@ -123,6 +130,7 @@ __global__ void __launch_bounds__((CWARPS + 1) * 32, MINB) rowblock_kernel(const
                 }
             }
         }
+        if (lane == 0) drain_fills<STAGES>(c.full, fills, role_limit, hdr);
     } else {
         T* out = static_cast<T*>(p.out);
         const bool excl = p.exclusive != 0;

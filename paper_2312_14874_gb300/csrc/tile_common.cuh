@@ -161,10 +161,47 @@ __device__ __forceinline__ void thread_outputs(const typename Op::T (&x)[ITEMS],
         thread_outputs_t<Op, ITEMS, HEADS, false>(x, hm, gv, y);
 }
 
+// The part of staging a tile that the lanes of one warp do when the tile is
+// not a whole, aligned tile (a ragged last tile, or arrays that are not
+// 16-byte aligned).  Elements [0, cnt) of src go to dst.  With `bulk_ok` (src
+// and dst 16-byte aligned) the largest 16-byte multiple prefix is left to one
+// bulk copy that the caller issues on its barrier: its byte count is
+// returned.  The lanes copy the rest with B loads in flight each (one
+// dependent load at a time made a ragged tile cost about 15 us, which then
+// gated the end of every launch), and write `pad` into [cnt, fill).  The
+// caller orders these generic writes before its barrier arrive (__syncwarp).
+template <class T>
+__device__ __forceinline__ uint32_t warp_stage_partial(T* dst, const T* src, int cnt, int fill,
+                                                       bool bulk_ok, T pad, int lane) {
+    constexpr int B = 16;
+    const uint32_t bulk =
+        bulk_ok ? (static_cast<uint32_t>(cnt) * static_cast<uint32_t>(sizeof(T))) & ~15u : 0u;
+    const int first = static_cast<int>(bulk / sizeof(T));
+    for (int base = first; base < cnt; base += 32 * B) {
+        T v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = base + b * 32 + lane;
+            if (i < cnt) v[b] = src[i];
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int i = base + b * 32 + lane;
+            if (i < cnt) dst[i] = v[b];
+        }
+    }
+    for (int i = cnt + lane; i < fill; i += 32) dst[i] = pad;
+    return bulk;
+}
+
 template <int NTHREADS>
 __device__ __forceinline__ void named_barrier_sync(int id) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NTHREADS) : "memory");
 }
+
+#ifndef GBSCAN_SUSPEND_NS
+#define GBSCAN_SUSPEND_NS 20000u
+#endif
 
 // Bounded mbarrier wait; returns false if the phase did not complete within
 // the limit (or, with epoch != 0, once the launch has been aborted by another
@@ -172,10 +209,19 @@ __device__ __forceinline__ void named_barrier_sync(int id) {
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns, Header* hdr, uint32_t epoch,
                                                   bool report) {
+#ifdef GBSCAN_WAIT_POLL
+    if (mbar_test_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    uint32_t polls = 0;
+    while (!mbar_test_wait(bar, parity)) {
+        __nanosleep(64);
+        if ((polls & 31) != 31) { ++polls; continue; }
+#else
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     uint32_t polls = 0;
-    while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
+    while (!mbar_try_wait_sleep(bar, parity, GBSCAN_SUSPEND_NS)) {
+#endif
         if ((++polls & 7) == 0 && epoch != 0 && launch_aborted(hdr, epoch)) return false;
         if (global_timer_ns() - t0 > limit_ns) {
             if (report) {
@@ -207,6 +253,24 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Before a block exits, the bulk copies it started into shared memory must
+// have landed: a copy still in flight would write into shared memory that the
+// next block on the SM may own.  The loader calls this once its loop has
+// ended, with fills = the number of times it filled the stages in order (fill
+// k went to stage k % STAGES and completes phase k / STAGES of full[stage]).
+// Only the last fill of each stage can still be pending: a stage is refilled
+// only after its previous fill was consumed.  Each wait is bounded; one that
+// runs out is recorded (an earlier error is kept).
+template <int STAGES>
+__device__ __forceinline__ void drain_fills(uint64_t* full, uint32_t fills, uint64_t limit_ns,
+                                            Header* hdr) {
+    for (int s = 0; s < STAGES; ++s) {
+        if (static_cast<uint32_t>(s) >= fills) break;
+        const uint32_t last = (fills - 1 - static_cast<uint32_t>(s)) / STAGES * STAGES + s;
+        mbar_wait_bounded(&full[s], (last / STAGES) & 1u, limit_ns, hdr, 0, true);
+    }
 }
 
 // Warp-uniform dispatch for segmented kinds.  The flagged versions cost

@@ -119,24 +119,65 @@ def test_race_stress_partitioned_small_chunks(tmp_path, lag):
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
 
 
-@pytest.mark.parametrize("algo", ["single_pass", "partitioned"])
+# With a 2 ms spin limit, a launch that runs into a bounded wait must end
+# within its normal time plus the bounds it can meet in sequence: the first
+# wait to run out (a look-back or status wait: one spin limit; a pipeline wait:
+# 4 spin limits + 10 ms) aborts the launch, the claim counter is poisoned, and
+# every other wait then gives up within about 160 us.  One second is far above
+# that and far below what a wait that ignored the abort would cost.
+LAUNCH_BOUND_S = 1.0
+
+
+@pytest.mark.parametrize("algo", ["single_pass", "partitioned", "two_pass"])
 @pytest.mark.parametrize("dtype", [torch.int32, torch.int64, torch.float32])
 def test_dropped_tile_times_out_and_recovers(dtype, algo):
     """A tile that never publishes (the drop hook) makes the waits on it run out:
     the single-pass look-back of later tiles, or the partitioned scan's chunk
-    scan and the second pass behind it.  The launch ends with TIMEOUT recorded,
-    and the same workspace works again once the hook is removed."""
+    scan and the second pass behind it; in the two-pass scan, whose blocks
+    never wait for one another, the hook instead leaves the tile's stage load
+    unissued, so that stage never fills.  The launch ends with TIMEOUT recorded,
+    within the bound above, and the same workspace works again once the hook is
+    removed."""
+    import time
     n = 50 * 5120
     ws = gb.Workspace(gb.workspace_bytes(dtype, _capi.KIND_SCAN, n))
     x = torch.ones(n, dtype=dtype, device=dev())
     gb.set_debug(spin_limit_us=2000, drop_tile=17, workspace=ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     gb.inclusive(x, workspace=ws, algo=algo)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < LAUNCH_BOUND_S
     assert gb.device_status(ws) == _capi.ERR_TIMEOUT
     assert gb.device_status(ws) == 0  # cleared by the read
     # the workspace is usable again once the hook is removed
     gb.set_debug(workspace=ws)
     y = gb.inclusive(x, workspace=ws, algo=algo)
     assert torch.equal(y.long(), torch.arange(1, n + 1, device=dev()))
+    assert gb.device_status(ws) == 0
+
+
+def test_two_pass_compensated_stage_never_fills():
+    """The compensated fp32 scan (two-pass under AUTO) with one stage load never
+    issued, at 2^22 elements (hundreds of tiles per block): the block whose
+    stage never fills stops at once instead of paying the bound on every later
+    tile; both passes end within the bound with TIMEOUT, and the next call on
+    the same workspace is correct again."""
+    import time
+    n = 1 << 22
+    ws = gb.Workspace(gb.workspace_bytes(torch.float32, _capi.KIND_SCAN, n))
+    x = torch.ones(n, dtype=torch.float32, device=dev())
+    gb.set_debug(spin_limit_us=2000, drop_tile=3, workspace=ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        gb.inclusive(x, workspace=ws, compensated=True, algo="two_pass")
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 3 * LAUNCH_BOUND_S
+    assert gb.device_status(ws) == _capi.ERR_TIMEOUT
+    gb.set_debug(workspace=ws)
+    y = gb.inclusive(x, workspace=ws, compensated=True, algo="two_pass")
+    assert torch.equal(y, torch.arange(1, n + 1, device=dev(), dtype=torch.float32))
     assert gb.device_status(ws) == 0
 
 
