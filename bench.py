@@ -59,6 +59,14 @@ def parse_args(argv=None):
     ap.add_argument("--n-log2", type=int, default=N_LOG2,
                     help="array size 2^k (profiling runs use a smaller case; the benchmark "
                          "workload is 2^30)")
+    prof = ap.add_argument_group("profiler targets (no timing, no JSON line)")
+    prof.add_argument("--profile-case", choices=["scan", "seg_f32", "compact_i32"],
+                      help="launch one workload --reps times and exit: a target for ncu")
+    prof.add_argument("--dtype", choices=["i32", "i64", "f32", "f32c"], default="i32",
+                      help="scan case: element type (f32c = compensated fp32)")
+    prof.add_argument("--n", type=int, default=None, help="scan case: element count (else 2^--n-log2)")
+    prof.add_argument("--variant", type=int, default=None, help="scan case: launch shape (else tuned)")
+    prof.add_argument("--reps", type=int, default=4, help="launches of the case")
     return ap.parse_args(argv)
 
 
@@ -430,12 +438,78 @@ def side_measurements(dev, peak) -> dict:
     return res
 
 
+# ---- profiler targets -------------------------------------------------------------
+
+def profile_case(args) -> int:
+    """One workload launched --reps times, for a profiler: every launch is the
+    same; the first ones warm the caches and load the module, so a profiler
+    skips them.  Inputs are seeded and synthetic; nothing is checked here (the
+    test suite does that).
+
+    scan         the plain inclusive scan of --dtype, 2^--n-log2 (or --n)
+                 elements, U[0,1) for floats, with --algo and --variant (tuned
+                 when not given)
+    seg_f32      the exclusive segmented scan of 20,000 segments with lengths
+                 log-uniform in [1, 2^16] (116,893,251 fp32 elements, U[0,1))
+    compact_i32  stream compaction of 2^28 int32 elements with half kept
+    """
+    import torch
+    import paper_2312_14874_gb300 as gb
+    from paper_2312_14874_gb300 import _capi
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    if args.profile_case == "scan":
+        dt = {"i32": torch.int32, "i64": torch.int64, "f32": torch.float32, "f32c": torch.float32}[args.dtype]
+        n = args.n if args.n is not None else 1 << args.n_log2
+        if dt.is_floating_point:
+            x = torch.rand(n, device=dev, generator=g)
+        else:
+            x = torch.randint(0, 256, (n,), dtype=dt, device=dev, generator=g)
+        y = torch.empty_like(x)
+        ws = gb.Workspace(gb.workspace_bytes(dt, _capi.KIND_SCAN, n), dev)
+        for _ in range(args.reps):
+            gb.inclusive(x, out=y, workspace=ws, algo=args.algo, variant=args.variant,
+                         compensated=args.dtype == "f32c")
+        torch.cuda.synchronize(dev)
+        print(f"scan {args.dtype}: n={n}, algo={args.algo}, variant={args.variant}, "
+              f"launches={args.reps}, status={gb.device_status(ws, dev)}")
+    elif args.profile_case == "seg_f32":
+        import synth
+        off = synth.segment_offsets(20000, max_log2=16, seed=0)
+        n = int(off[-1])
+        x = torch.rand(n, device=dev, generator=g)
+        y = torch.empty_like(x)
+        o = torch.from_numpy(off).to(dev)
+        ws = gb.Workspace(gb.workspace_bytes(torch.float32, _capi.KIND_SEGMENTED, n, off.size - 1), dev)
+        for _ in range(args.reps):
+            gb.segmented(x, o, True, out=y, workspace=ws)
+        torch.cuda.synchronize(dev)
+        print(f"seg_f32: n={n}, segments={off.size - 1}, launches={args.reps}, "
+              f"status={gb.device_status(ws, dev)}")
+    else:
+        n = 1 << 28
+        x = torch.randint(0, 1 << 30, (n,), dtype=torch.int32, device=dev, generator=g)
+        flags = (torch.rand(n, device=dev, generator=g) < 0.5).view(torch.uint8)
+        y = torch.empty_like(x)
+        ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_COMPACT, n), dev)
+        count = None
+        for _ in range(args.reps):
+            _, count = gb.compact(x, flags, out=y, workspace=ws)
+        torch.cuda.synchronize(dev)
+        print(f"compact_i32: n={n}, kept={int(count.item())}, launches={args.reps}, "
+              f"status={gb.device_status(ws, dev)}")
+    return 0
+
+
 # ---- main ------------------------------------------------------------------------
 
 def main(argv=None) -> int:
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return profile_case(args)
 
     import numpy as np
     import torch

@@ -295,10 +295,15 @@ int gbscan_abi_version(void);
  * GBSCAN_NOALLOC_MAX_N elements; larger n returns GBSCAN_ERR_UNSUPPORTED and
  * launches nothing.
  *   in, out : device arrays of n int32 (out == in allowed), owned by the caller.
- *   n       : 0 <= n <= GBSCAN_NOALLOC_MAX_N; n == 0 is a no-op.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call clears the array's launch counters and error
+ *   n       : 0 <= n <= GBSCAN_NOALLOC_MAX_N; n == 0 scans nothing.
+ * The first call on a device (n == 0 is enough: a warm-up call) looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current, and
+ * may make CUDA load the library's device code and the array at that moment,
+ * which allocates device memory.  So make one call per device at
+ * initialisation, outside any no-allocation context and before any stream
+ * capture.  Argument errors (null, misaligned or partly overlapping buffers)
+ * return before the array is touched.  Every call clears the array's launch
+ * counters and error
  * word (cudaMemsetAsync on `stream`), so device-side errors (bounded waits
  * that ran out) are not reported by this entry point.  All calls share the one
  * array: calls whose executions overlap on the GPU (other streams, or other

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbscan_launch.cuh"
 
 namespace gbscan {
@@ -124,6 +126,17 @@ __global__ void __launch_bounds__(256) copy_kernel(const uint4* __restrict__ src
 
 namespace {
 
+// An NVTX range around each C-ABI call that launches work, named after the
+// entry point, so that a profiler's timeline shows which call a kernel came
+// from.  Without a tool attached a range costs a pointer test.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define GBSCAN_NVTX_RANGE(name) NvtxRange gbscan_nvtx_range_(name)
+
 constexpr size_t kHeaderBytes = sizeof(Header);
 constexpr int64_t kMaxTiles = (int64_t(1) << 31) - (int64_t(1) << 24);
 
@@ -135,11 +148,20 @@ bool valid_dtype(int dt) { return dt >= GBSCAN_I32 && dt <= GBSCAN_F64; }
 
 // Records needed for n elements at tile size `tile`: one per tile plus the
 // segment locator's end sentinel; they come in blocks of 16.
-int64_t records_for(int64_t n, int tile) { return (n + tile - 1) / tile + 1; }
+constexpr int64_t records_for(int64_t n, int tile) { return (n + tile - 1) / tile + 1; }
 
-size_t record_bytes(int64_t records) {
+constexpr size_t record_bytes(int64_t records) {
     return static_cast<size_t>((records + 15) / 16) * kRecBlockBytes;
 }
+
+// scan_inclusive_i32_noalloc runs the int32 plain family's variant 0 (8
+// consumer warps x 20 items); its scratch must hold the header and that
+// tile's records for GBSCAN_NOALLOC_MAX_N elements.  The tile is checked
+// against the variant table when the entry point runs.
+constexpr int kNoallocTile = 8 * 32 * 20;
+static_assert(sizeof(Header) + record_bytes(records_for(GBSCAN_NOALLOC_MAX_N, kNoallocTile)) <=
+                  GBSCAN_NOALLOC_SCRATCH_BYTES,
+              "the no-allocation scratch must hold GBSCAN_NOALLOC_MAX_N elements' records");
 
 // The head bitmap of a segmented scan sits after the largest record region a
 // call on n elements of this size can use, and covers every variant's last
@@ -430,6 +452,7 @@ gbscan_status gbscan_workspace_size(gbscan_dtype dtype, gbscan_kind kind, int64_
 }
 
 gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("gbscan_workspace_init");
     if (ws == nullptr || ws_bytes < kHeaderBytes) return GBSCAN_ERR_WORKSPACE;
     return from_cuda(cudaMemsetAsync(ws, 0, ws_bytes, stream));
 }
@@ -437,6 +460,7 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
 #define GBSCAN_FLAT(NAME, TYPE, FAMILY, EXCL)                                                  \
     gbscan_status NAME(const TYPE* in, TYPE* out, int64_t n, void* ws, size_t ws_bytes,       \
                        gbscan_algo algo, int variant, cudaStream_t stream) {                  \
+        GBSCAN_NVTX_RANGE(#NAME);                                                             \
         return scan_flat(FAMILY(), in, out, n, sizeof(TYPE), EXCL, ws, ws_bytes, algo, variant, \
                          stream);                                                             \
     }
@@ -460,12 +484,14 @@ static gbscan_status scan_f32_impl(const float* in, float* out, int64_t n, gbsca
 gbscan_status scan_inclusive_f32(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
                                  void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                                  cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_inclusive_f32");
     return scan_f32_impl(in, out, n, mode, 0, ws, ws_bytes, algo, variant, stream);
 }
 
 gbscan_status scan_exclusive_f32(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
                                  void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                                  cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_exclusive_f32");
     return scan_f32_impl(in, out, n, mode, 1, ws, ws_bytes, algo, variant, stream);
 }
 
@@ -475,6 +501,7 @@ constexpr int64_t kHostPieceElems = 16ll << 20;
 gbscan_status scan_inclusive_i32_host(const int32_t* h_in, int32_t* h_out, int64_t n,
                                       int32_t* d_buf, int64_t d_elems, void* ws, size_t ws_bytes,
                                       cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_inclusive_i32_host");
     if (n < 0 || d_elems < 0) return GBSCAN_ERR_INVALID_ARG;
     if (n == 0) return GBSCAN_OK;
     if (h_in == nullptr || h_out == nullptr || d_buf == nullptr) return GBSCAN_ERR_INVALID_ARG;
@@ -560,18 +587,21 @@ gbscan_status scan_inclusive_i32_host(const int32_t* h_in, int32_t* h_out, int64
 gbscan_status compact_i32(const int32_t* in, const uint8_t* flags, int32_t* out, int64_t n,
                           int64_t* count, void* ws, size_t ws_bytes, int variant,
                           cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("compact_i32");
     return compact_impl(in, flags, out, n, count, ws, ws_bytes, variant, stream);
 }
 
 gbscan_status compact_f32(const float* in, const uint8_t* flags, float* out, int64_t n,
                           int64_t* count, void* ws, size_t ws_bytes, int variant,
                           cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("compact_f32");
     return compact_impl(in, flags, out, n, count, ws, ws_bytes, variant, stream);
 }
 
 gbscan_status scan_op_i32(const int32_t* in, int32_t* out, int64_t n, gbscan_op op,
                           int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo,
                           int variant, cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_op_i32");
     const Family* fam = op == GBSCAN_OP_SUM ? &family_scan_i32()
                         : op == GBSCAN_OP_MAX ? &family_max_i32()
                         : op == GBSCAN_OP_MIN ? &family_min_i32()
@@ -584,6 +614,7 @@ gbscan_status scan_op_i32(const int32_t* in, int32_t* out, int64_t n, gbscan_op 
 gbscan_status scan_op_f32(const float* in, float* out, int64_t n, gbscan_op op, int exclusive,
                           void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                           cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_op_f32");
     const Family* fam = op == GBSCAN_OP_SUM ? &family_scan_f32()
                         : op == GBSCAN_OP_MAX ? &family_max_f32()
                         : op == GBSCAN_OP_MIN ? &family_min_f32()
@@ -597,6 +628,7 @@ gbscan_status scan_segmented_batched_i32(const int32_t* in, int32_t* out, int64_
                                          const int64_t* offsets, int64_t num_segments,
                                          int exclusive, void* ws, size_t ws_bytes, int variant,
                                          cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_segmented_batched_i32");
     return scan_seg_impl(family_seg_i32(), in, out, n, offsets, num_segments, sizeof(int32_t),
                          exclusive != 0, ws, ws_bytes, variant, stream);
 }
@@ -605,6 +637,7 @@ gbscan_status scan_segmented_batched_f32(const float* in, float* out, int64_t n,
                                          const int64_t* offsets, int64_t num_segments,
                                          int exclusive, void* ws, size_t ws_bytes, int variant,
                                          cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_segmented_batched_f32");
     return scan_seg_impl(family_seg_f32(), in, out, n, offsets, num_segments, sizeof(float),
                          exclusive != 0, ws, ws_bytes, variant, stream);
 }
@@ -612,6 +645,7 @@ gbscan_status scan_segmented_batched_f32(const float* in, float* out, int64_t n,
 gbscan_status scan_rows_f32(const float* in, float* out, int64_t rows, int64_t cols,
                             int exclusive, void* ws, size_t ws_bytes, int variant,
                             cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_rows_f32");
     return scan_rows_impl(family_rows_f32(), in, out, rows, cols, sizeof(float), exclusive != 0,
                           ws, ws_bytes, variant, stream);
 }
@@ -619,6 +653,7 @@ gbscan_status scan_rows_f32(const float* in, float* out, int64_t rows, int64_t c
 gbscan_status scan_rows_f64(const double* in, double* out, int64_t rows, int64_t cols,
                             int exclusive, void* ws, size_t ws_bytes, int variant,
                             cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_rows_f64");
     return scan_rows_impl(family_rows_f64(), in, out, rows, cols, sizeof(double), exclusive != 0,
                           ws, ws_bytes, variant, stream);
 }
@@ -626,6 +661,7 @@ gbscan_status scan_rows_f64(const double* in, double* out, int64_t rows, int64_t
 gbscan_status scan_backward_f32(const float* grad_out, float* grad_in, int64_t rows, int64_t cols,
                                 int exclusive, void* ws, size_t ws_bytes, int variant,
                                 cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_backward_f32");
     return scan_rows_impl(family_rows_rev_f32(), grad_out, grad_in, rows, cols, sizeof(float),
                           exclusive != 0, ws, ws_bytes, variant, stream);
 }
@@ -633,11 +669,13 @@ gbscan_status scan_backward_f32(const float* grad_out, float* grad_in, int64_t r
 gbscan_status scan_backward_f64(const double* grad_out, double* grad_in, int64_t rows,
                                 int64_t cols, int exclusive, void* ws, size_t ws_bytes,
                                 int variant, cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_backward_f64");
     return scan_rows_impl(family_rows_rev_f64(), grad_out, grad_in, rows, cols, sizeof(double),
                           exclusive != 0, ws, ws_bytes, variant, stream);
 }
 
 gbscan_status scan_get_device_status(void* ws, cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_get_device_status");
     if (ws == nullptr) return GBSCAN_ERR_WORKSPACE;
     Header* hdr = static_cast<Header*>(ws);
     if (cudaStreamSynchronize(stream) != cudaSuccess) return GBSCAN_ERR_CUDA;
@@ -654,6 +692,7 @@ gbscan_status scan_get_device_status(void* ws, cudaStream_t stream) {
 
 gbscan_status gbscan_set_debug(void* ws, size_t ws_bytes, uint32_t spin_limit_us,
                                int64_t drop_tile, uint32_t delay_ns_max, cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("gbscan_set_debug");
     if (ws == nullptr || ws_bytes < kHeaderBytes) return GBSCAN_ERR_WORKSPACE;
     cudaGetLastError();
     set_debug_kernel<<<1, 1, 0, stream>>>(static_cast<Header*>(ws), spin_limit_us, drop_tile,
@@ -682,6 +721,7 @@ gbscan_status gbscan_variant_info(gbscan_dtype dtype, gbscan_kind kind, int vari
 }
 
 gbscan_status gbscan_copy(const void* src, void* dst, size_t bytes, cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("gbscan_copy");
     if (bytes == 0) return GBSCAN_OK;
     if (src == nullptr || dst == nullptr) return GBSCAN_ERR_INVALID_ARG;
     if (ranges_overlap(src, bytes, dst, bytes)) return GBSCAN_ERR_INVALID_ARG;
@@ -734,17 +774,21 @@ static void* noalloc_scratch_address(int device) {
 
 gbscan_status scan_inclusive_i32_noalloc(const int32_t* in, int32_t* out, int64_t n,
                                          cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_inclusive_i32_noalloc");
     if (n < 0) return GBSCAN_ERR_INVALID_ARG;
     if (n > GBSCAN_NOALLOC_MAX_N) return GBSCAN_ERR_UNSUPPORTED;
-    if (n == 0) return GBSCAN_OK;
     const Family& fam = family_scan_i32();
-    const int64_t records = records_for(n, fam.variants[0].tile);
-    if (kHeaderBytes + record_bytes(records) > GBSCAN_NOALLOC_SCRATCH_BYTES)
-        return GBSCAN_ERR_UNSUPPORTED;
+    if (fam.variants[0].tile != kNoallocTile) return GBSCAN_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GBSCAN_ERR_CUDA;
+    // the per-device address lookup, also for n == 0 (a warm-up call)
     void* ws = noalloc_scratch_address(dev);
     if (ws == nullptr) return GBSCAN_ERR_CUDA;
+    if (n == 0) return GBSCAN_OK;
+    // the same argument checks as the scan itself, before the shared array is
+    // touched: a call that is rejected changes nothing in it
+    gbscan_status st = check_io(in, out, n, sizeof(int32_t));
+    if (st != GBSCAN_OK) return st;
     // Launch state that must start at zero: the tile and done counters and the
     // error word (header bytes 4..15).  The epoch (bytes 0..3) is kept: it is
     // what makes the status records of earlier calls stale.

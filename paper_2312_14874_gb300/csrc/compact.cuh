@@ -250,7 +250,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             if (lane == 0) {
                 c.tile_id[s] = t;
                 c.phase[s] = phase;
-                const uint32_t stat_bytes = phase == kItemScan ? 48u : 0u;
+                const uint32_t stat_bytes = phase == kItemScan ? 32u : 0u;
                 const uint32_t tx = fbytes + xbytes + stat_bytes;
                 if (tx == 0) {
                     mbar_arrive(&c.full[s]);
@@ -260,10 +260,10 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                         bulk_load_hint(fb, fl + f0, fbytes, &c.full[s], phase == kItemReduce ? keep : drop);
                     if (xbytes) bulk_load_hint(xb, in + t * TILE, xbytes, &c.full[s], drop);
                     if (stat_bytes) {
-                        bulk_load(&c.stat[s][0], rec_lo(p.rec, t & ~int64_t(1)), 16, &c.full[s]);
+                        // the tile's status pair and the chunk's E pair
+                        bulk_load(&c.stat[s][0], rec_tile<OpI64>(p.rec, t), 16, &c.full[s]);
                         const uint32_t ch = static_cast<uint32_t>(t) / order.K;
                         bulk_load(&c.stat[s][4], rec_chunk(p.rec, ch, 0), 16, &c.full[s]);
-                        bulk_load(&c.stat[s][2], rec_hi(p.rec, t & ~int64_t(1)), 16, &c.full[s]);
                     }
                 }
             }
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                     uint32_t se, so;
                     bool hf;
                     parse_words<Op>(c.stat[s][4], c.stat[s][5], epoch, se, hf, e);
-                    parse_words<Op>(c.stat[s][ts & 1], c.stat[s][2 + (ts & 1)], epoch, so, hf, off);
+                    parse_words<Op>(c.stat[s][0], c.stat[s][1], epoch, so, hf, off);
                     const uint64_t t0 = global_timer_ns();
                     while (se != kStateP || so != kStateP) {
                         if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
@@ -302,9 +302,9 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                         __nanosleep(64);
                         poll_round_fence();
                         if (se != kStateP)
-                            read_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, se, hf, e);
+                            read_words<Op>(rec_chunk(p.rec, ch, 0), epoch, se, hf, e);
                         if (so != kStateP)
-                            read_words<Op>(rec_lo(p.rec, ts), rec_hi(p.rec, ts), epoch, so, hf, off);
+                            read_words<Op>(rec_tile<Op>(p.rec, ts), epoch, so, hf, off);
                     }
                     c.base = e + off;
                 }

@@ -126,7 +126,10 @@ __device__ __forceinline__ bool warp_spin_wait(uint64_t* bar, uint32_t parity, u
 }
 
 // Sum of a whole stage by one warp: consecutive lanes on consecutive 16-byte
-// vectors, SU vectors in flight per lane with independent partial sums.
+// vectors, SU vectors in flight per lane with independent partial sums; each
+// vector is summed on its own (a run of VEC elements) and joined to its
+// partial sum with `combine`, so compensated pairs see runs of at most four
+// plain additions.
 template <class Op, int TILE, int SU>
 __device__ __forceinline__ typename Op::Acc stage_sum(const unsigned char* stage, int lane) {
     using T = typename Op::T;
@@ -149,8 +152,10 @@ __device__ __forceinline__ typename Op::Acc stage_sum(const unsigned char* stage
         for (int u = 0; u < U; ++u) {
             if (q0 + u < PER_LANE) {
                 const T* e = reinterpret_cast<const T*>(&w[u]);
+                Acc vs = Op::lift(e[0]);
 #pragma unroll
-                for (int j = 0; j < VEC; ++j) Op::accumulate(part[u], e[j]);
+                for (int j = 1; j < VEC; ++j) Op::accumulate(vs, e[j]);
+                part[u] = Op::combine(part[u], vs);
             }
         }
     }

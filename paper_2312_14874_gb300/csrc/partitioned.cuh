@@ -107,9 +107,9 @@ struct PtCtrl {
     uint64_t empty[STAGES];
     int64_t tile_id[STAGES];
     uint32_t phase[STAGES];
-    // per stage, for a scan item: copies of the tile's status word pair (the
-    // 16-byte pair holding lo[t], and the one holding hi[t]) and of the chunk's
-    // E words, brought in by the loader's bulk copies
+    // per stage, for a scan item: copies of the 16-byte unit holding the
+    // tile's status word (or pair) and of the chunk's E pair, brought in by
+    // the loader's bulk copies
     alignas(16) unsigned long long stat[STAGES][6];
     // segmented scans: per stage, the tile's slice of the head bitmap (bit i =
     // element i starts a segment), then zero words for the reads past its end
@@ -174,9 +174,11 @@ __device__ __forceinline__ void chunk_rows_issue(const unsigned long long* rec, 
         w0[q] = 0ull;
         w1[q] = 0ull;
         if (i < nch) {
-            w0[q] = ld_poll_u64(rec_lo(const_cast<unsigned long long*>(rec), first + i));
-            if constexpr (!Op::kPacked)
-                w1[q] = ld_poll_u64(rec_hi(const_cast<unsigned long long*>(rec), first + i));
+            const unsigned long long* w = rec_tile<Op>(const_cast<unsigned long long*>(rec), first + i);
+            if constexpr (Op::kPacked)
+                w0[q] = ld_poll_u64(w);
+            else
+                ld_poll_pair(w, w0[q], w1[q]);
         }
     }
 }
@@ -232,7 +234,7 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
             for (int q = 0; q < R; ++q) {
                 if (st[q] == kStateX) {
                     const int64_t i = first + r0 + q * 32 + lane;
-                    read_words<Op>(rec_lo(p.rec, i), rec_hi(p.rec, i), epoch, st[q], hfl[q], v[q]);
+                    read_words<Op>(rec_tile<Op>(p.rec, i), epoch, st[q], hfl[q], v[q]);
                 }
             }
         }
@@ -293,7 +295,7 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
             uint32_t st = kStateX;
             const uint64_t t0 = global_timer_ns();
             while (true) {
-                read_words<Op>(rec_chunk(p.rec, ch - 1, 2), rec_chunk(p.rec, ch - 1, 3), epoch, st, ef, e);
+                read_words<Op>(rec_chunk(p.rec, ch - 1, 2), epoch, st, ef, e);
                 if (st == kStateP) break;
                 if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
                     record_timeout(hdr, epoch, first);
@@ -307,14 +309,14 @@ __device__ void chunk_scan_warp(const Params& p, int64_t ch, Header* hdr, uint32
             const uint32_t dly = mix32(static_cast<uint64_t>(ch) * 0x2545f4914f6cdd1dull) % (cfg.delay_max + 1);
             if (dly) __nanosleep(dly);
         }
-        publish_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, kStateP, ef, e);
+        publish_words<Op>(rec_chunk(p.rec, ch, 0), epoch, kStateP, ef, e);
         bool pf = carry_f;
         Acc pv = carry;
         if constexpr (HEADS != kNoHeads)
             seg_combine<Op>(ef, e, pf, pv);
         else
             pv = Op::combine(e, carry);
-        publish_words<Op>(rec_chunk(p.rec, ch, 2), rec_chunk(p.rec, ch, 3), epoch, kStateP, pf, pv);
+        publish_words<Op>(rec_chunk(p.rec, ch, 2), epoch, kStateP, pf, pv);
         // the last chunk's inclusive prefix is the total (stream compaction:
         // the number of elements kept)
         if (p.total_out != nullptr && first + nch == p.num_tiles)
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
             if (lane == 0) {
                 c.tile_id[s] = t;
                 c.phase[s] = phase;
-                const uint32_t stat_bytes = phase == kItemScan ? (Op::kPacked ? 32u : 48u) : 0u;
+                const uint32_t stat_bytes = phase == kItemScan ? 32u : 0u;
                 const uint32_t tx = body + stat_bytes + BITS_BYTES;
                 if (tx == 0) {
                     mbar_arrive(&c.full[s]);
@@ -439,13 +441,13 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     if constexpr (HEADS != kNoHeads)
                         bulk_load(&c.bits[s][0], p.bitmap + t * (TILE / 32), BITS_BYTES, &c.full[s]);
                     if (stat_bytes) {
-                        // the 16-byte pairs holding the tile's status words, and E
-                        unsigned long long* pair = rec_lo(p.rec, t & ~int64_t(1));
-                        bulk_load(&c.stat[s][0], pair, 16, &c.full[s]);
+                        // the 16-byte unit holding the tile's status word (its
+                        // pair for 8-byte accumulators), and the chunk's E pair
+                        unsigned long long* unit =
+                            Op::kPacked ? rec_tile<Op>(p.rec, t & ~int64_t(1)) : rec_tile<Op>(p.rec, t);
+                        bulk_load(&c.stat[s][0], unit, 16, &c.full[s]);
                         const uint32_t ch = static_cast<uint32_t>(t) / order.K;
                         bulk_load(&c.stat[s][4], rec_chunk(p.rec, ch, 0), 16, &c.full[s]);
-                        if (!Op::kPacked)
-                            bulk_load(&c.stat[s][2], rec_hi(p.rec, t & ~int64_t(1)), 16, &c.full[s]);
                     }
                 }
             }
@@ -592,7 +594,10 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 uint32_t se, so;
                 bool ef, of;
                 parse_words<Op>(c.stat[s][4], c.stat[s][5], epoch, se, ef, e);
-                parse_words<Op>(c.stat[s][t & 1], c.stat[s][2 + (t & 1)], epoch, so, of, off);
+                if constexpr (Op::kPacked)
+                    parse_words<Op>(c.stat[s][t & 1], 0ull, epoch, so, of, off);
+                else
+                    parse_words<Op>(c.stat[s][0], c.stat[s][1], epoch, so, of, off);
                 const uint64_t t0 = global_timer_ns();
                 while (se != kStateP || so != kStateP) {
                     if (global_timer_ns() - t0 > cfg.spin_limit_ns || launch_aborted(hdr, epoch)) {
@@ -602,9 +607,9 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     __nanosleep(64);
                     poll_round_fence();
                     if (se != kStateP)
-                        read_words<Op>(rec_chunk(p.rec, ch, 0), rec_chunk(p.rec, ch, 1), epoch, se, ef, e);
+                        read_words<Op>(rec_chunk(p.rec, ch, 0), epoch, se, ef, e);
                     if (so != kStateP)
-                        read_words<Op>(rec_lo(p.rec, t), rec_hi(p.rec, t), epoch, so, of, off);
+                        read_words<Op>(rec_tile<Op>(p.rec, t), epoch, so, of, off);
                 }
                 // the tile's carry: the chunk prefix, then the in-chunk offset
                 if constexpr (HEADS != kNoHeads) {

@@ -81,10 +81,35 @@ __device__ __forceinline__ uint32_t row_heads(int64_t tb, int cnt, int64_t cols,
 }
 
 // Sequential reduction of the thread's items; a head restarts the sum.
+// Operators whose accumulation is a long dependent chain (Op::kSplit > 1, the
+// compensated TwoSum pairs) sum a thread's items as kSplit contiguous
+// sub-blocks in independent chains, combined once at the end: the chain a
+// thread waits for is ITEMS / kSplit accumulations long instead of ITEMS.
+template <class Op, int ITEMS>
+__device__ __forceinline__ void split_sums(const typename Op::T (&x)[ITEMS],
+                                           typename Op::Acc (&part)[Op::kSplit]) {
+    constexpr int K = Op::kSplit, L = ITEMS / K;
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[k] = Op::lift(x[k * L]);
+#pragma unroll
+    for (int j = 1; j < L; ++j) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) Op::accumulate(part[k], x[k * L + j]);
+    }
+}
+
 template <class Op, int ITEMS, int HEADS>
 __device__ __forceinline__ void thread_reduce(const typename Op::T (&x)[ITEMS], uint32_t hm,
                                               bool& f, typename Op::Acc& v) {
     f = false;
+    if constexpr (HEADS == kNoHeads && Op::kSplit > 1 && ITEMS % Op::kSplit == 0) {
+        typename Op::Acc part[Op::kSplit];
+        split_sums<Op, ITEMS>(x, part);
+        v = part[0];
+#pragma unroll
+        for (int k = 1; k < Op::kSplit; ++k) v = Op::combine(v, part[k]);
+        return;
+    }
     v = Op::identity();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
@@ -134,6 +159,30 @@ __device__ __forceinline__ void thread_outputs_t(const typename Op::T (&x)[ITEMS
                                                  typename Op::Acc gv, typename Op::T (&y)[ITEMS]) {
     using T = typename Op::T;
     using Acc = typename Op::Acc;
+    if constexpr (HEADS == kNoHeads && Op::kSplit > 1 && ITEMS % Op::kSplit == 0) {
+        // sub-block sums, the carry into each sub-block, then each sub-block's
+        // outputs from its own carry: K independent chains of ITEMS / K
+        constexpr int K = Op::kSplit, L = ITEMS / K;
+        Acc part[K];
+        split_sums<Op, ITEMS>(x, part);
+        Acc cin[K];
+        cin[0] = gv;
+#pragma unroll
+        for (int k = 1; k < K; ++k) cin[k] = Op::combine(cin[k - 1], part[k - 1]);
+        Acc r[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) r[k] = Op::identity();
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (EXCL) y[k * L + j] = Op::output(cin[k], r[k]);
+                Op::accumulate(r[k], x[k * L + j]);
+                if (!EXCL) y[k * L + j] = Op::output(cin[k], r[k]);
+            }
+        }
+        return;
+    }
     bool rf = false;
     Acc rv = Op::identity();
 #pragma unroll
