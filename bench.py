@@ -1,20 +1,25 @@
 """Benchmark: inclusive prefix sum of int32, n = 2^30, values uniform in
-[0, 255] (seed 0), single-pass chained scan on one GB300.
+[0, 255] (seed 0), on one GB300.
 
-One step = one pass of the whole scan (tile load, register/warp/block scan,
-look-back, carry add, store) over the 2^30-element array, one kernel launch.
-The metric is GB/s = (bytes read + bytes written) / device time, with
-8 * 2^30 bytes per step; inputs (4 GiB) and outputs are larger than the
+One step = one scan of the whole 2^30-element array with the algorithm and
+launch shape the autotuner picked for this GPU and size (the partitioned
+scan at 2^30: one persistent launch per step), tile load through carry add
+and store.  The metric is GB/s = (bytes read + bytes written) / device time,
+with 8 * 2^30 bytes per step; inputs (4 GiB) and outputs are larger than the
 129 MB L2, so no flush is needed between steps.
 
-Prints one JSON line (rank 0).  Extra fields: the roofline of the scan kernel
-against the measured HBM copy bandwidth, the end-to-end number through the
-public API with host buffers, SM clocks sampled during the timed region, the
-CPU oracle timed on a bounded sample (cpu_baseline), and side measurements of
-the other kernels (two-pass, int64, fp32 plain/compensated, segmented,
-row-wise forward/backward, device copy) at their own sizes.
+Prints one JSON line (rank 0).  Extra fields: the roofline of the timed
+kernel against the measured HBM copy bandwidth; the single-pass decoupled
+look-back kernel's own figure at the same size (north_star_single_pass); the
+end-to-end number through the public API with host buffers, next to a
+copy-only run of the same host-link schedule; SM clocks sampled during the
+timed region; the CPU oracle timed on a bounded sample (cpu_baseline); and
+side measurements of the other kernels (single-pass, two-pass, int64, fp32
+plain and compensated, segmented, row-wise forward/backward, compaction,
+device copy) at their own sizes.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --profile-case scan|seg_f32|compact_i32 ...   (profiler target)
 
 Under torchrun (N > 1) every rank runs its own replica on its own GPU (the
 scan does not shard here: replicas only); value = bytes of all ranks / the
@@ -373,7 +378,7 @@ def side_measurements(dev, peak) -> dict:
     nf = 1 << 28
     x = torch.randn(nf, device=dev)
     y = torch.empty_like(x)
-    for algo in ("single_pass", "partitioned"):
+    for algo in ("single_pass", "two_pass", "partitioned"):
         v = pick("scan_f32", nf, algo)
         rec(f"f32_2^28_plain_{algo}", 8 * nf, cuda_time_ms(
             lambda: gb.inclusive(x, out=y, workspace=ws, algo=algo, variant=v), reps)[0])
@@ -381,10 +386,14 @@ def side_measurements(dev, peak) -> dict:
         rec(f"f32_2^28_compensated_{algo}", 8 * nf, cuda_time_ms(
             lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True, algo=algo, variant=v),
             reps)[0])
+    # the algorithm AUTO runs for compensated fp32 at this size
+    rec("f32_2^28_compensated_auto", 8 * nf, cuda_time_ms(
+        lambda: gb.inclusive(x, out=y, workspace=ws, compensated=True), reps)[0])
     # fp32 max relative error of the tuned plain and compensated scans:
-    # max_k |y_k - ref_k| / sum_{i<=k} |a_i|, ref = a float64 cumsum on the GPU
-    # (its own error, about log2(n) * 2^-53 relative, is far below what is
-    # measured); on U[0,1) of the 2^-24 grid and on N(0,1)
+    # max_k |y_k - ref_k| / sum_{i<=k} |a_i|, with ref = torch.cumsum in
+    # float64 on the GPU (its own error, about log2(n) * 2^-53 relative, is far
+    # below what is measured; this run may not call the CPU oracle, which the
+    # full-size tests compare against); on U[0,1) of the 2^-24 grid and N(0,1)
     errs = {}
     for dist, make in (("uniform", lambda: torch.randint(0, 1 << 24, (nf,), device=dev).float() * 2.0 ** -24),
                        ("normal", lambda: torch.randn(nf, device=dev))):
@@ -399,7 +408,8 @@ def side_measurements(dev, peak) -> dict:
             errs[f"{dist}_{'compensated' if comp else 'plain'}"] = float(rel.max().item())
             del diff, rel
         del ref, den
-    res["fp32_max_rel_err"] = {"n": nf, "bounds": {"plain": 1e-5, "compensated": 1e-6}, **errs}
+    res["fp32_max_rel_err"] = {"n": nf, "bounds": {"plain": 1e-5, "compensated": 1e-6},
+                               "reference": "torch.cumsum of the input in float64 on the GPU", **errs}
     del x, y
     # segmented: 65,536 log-uniform segments in [1, 2^16], exclusive, CUDA graph
     off = synth.segment_offsets(65536, max_log2=16, seed=0)
@@ -578,6 +588,25 @@ def main(argv=None) -> int:
     ms_per_step = secs_max * 1e3 / args.steps
     achieved = BYTES_PER_STEP / (avg_launch_ms * 1e-3) / 1e9
 
+    # the single-pass decoupled look-back kernel at the same size, next to a
+    # device copy of the same bytes timed in the same run: the figure the
+    # single-pass target (85% of copy bandwidth at int32 2^30) is stated on
+    sp_variant = autotune.choose("scan_i32", "i32", N, "single_pass")[1]
+    sp_ms = cuda_time_ms(lambda: gb.inclusive(x, out=y, workspace=ws, algo="single_pass",
+                                              variant=sp_variant), 20)[0]
+    cp_ms = cuda_time_ms(lambda: y.copy_(x), 20)[0]
+    gb.inclusive(x, out=y, workspace=ws, algo="single_pass", variant=sp_variant)
+    torch.cuda.synchronize(dev)
+    if int(y[-1].item()) % (1 << 32) != total:
+        raise RuntimeError("single-pass result failed the last == total check")
+    north_star = {"kernel": "single-pass chained scan with decoupled look-back (lb_scan_kernel)",
+                  "variant": sp_variant, "ms": round(sp_ms, 4),
+                  "gbs": round(BYTES_PER_STEP / (sp_ms * 1e-3) / 1e9, 1),
+                  "copy_gbs_same_run": round(BYTES_PER_STEP / (cp_ms * 1e-3) / 1e9, 1),
+                  "frac_of_copy": round(cp_ms / sp_ms, 4),
+                  "frac_of_hbm": round(BYTES_PER_STEP / (sp_ms * 1e-3) / 1e9 / peak, 4),
+                  "target_frac_of_copy": 0.85}
+
     # end to end through the C ABI with host buffers (scan_inclusive_i32_host):
     # pinned host input -> device -> scan -> pinned host output, every step,
     # uploads, scans and downloads of 64 MiB pieces overlapping
@@ -602,9 +631,41 @@ def main(argv=None) -> int:
         if int(h_out[-1].item()) % (1 << 32) != total:
             raise RuntimeError("end-to-end result failed the last == total check")
         e2e_secs = max_over_ranks(a.elapsed_time(b) / 1e3 / e2e_steps, dev)
+        # the host link alone: the same pieces (64 MiB) uploaded into the same
+        # device buffer and downloaded again, upload and download overlapping
+        # on two streams as in the library's pipeline, no scan
+        piece = 16 << 20
+        s_dn = torch.cuda.Stream(dev)
+
+        def link_step():
+            for k0 in range(0, N, piece):
+                k1 = min(N, k0 + piece)
+                x[k0:k1].copy_(h_in[k0:k1], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                s_dn.wait_event(ev)
+                with torch.cuda.stream(s_dn):
+                    h_out[k0:k1].copy_(x[k0:k1], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s_dn)
+            stream.wait_event(ev)
+
+        link_step()
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for _ in range(e2e_steps):
+            link_step()
+        b.record(stream)
+        b.synchronize()
+        link_secs = max_over_ranks(a.elapsed_time(b) / 1e3 / e2e_steps, dev)
         e2e = {"value": round(aggregate(BYTES_PER_STEP, e2e_secs, world), 3), "unit": "GB/s",
                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
                "ms_per_step": round(e2e_secs * 1e3, 3),
+               "copy_only": {"value": round(aggregate(BYTES_PER_STEP, link_secs, world), 3), "unit": "GB/s",
+                             "ms_per_step": round(link_secs * 1e3, 3),
+                             "what": "the same 64 MiB pieces up and down through the same device buffer, "
+                                     "upload and download overlapping on two streams, no scan"},
+               "frac_of_copy_only": round(link_secs / e2e_secs, 4),
                "host_buffers": (f"pinned, allocated from {len(local_cpus)} CPUs local to the GPU (NVML)"
                                 if local_cpus else "pinned")}
         del h_out
@@ -658,6 +719,7 @@ def main(argv=None) -> int:
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"],
                        "power_w_max": clk.get("power_w_max")},
+            "north_star_single_pass": north_star,
             "cpu_baseline": cpu,
             "elements_per_s": round(value * 1e9 / 8, 1),
             "side": side,
