@@ -72,15 +72,23 @@ typedef enum {
     GBSCAN_F32_COMPENSATED = 1  /* per-thread and carried prefixes as (hi, lo) TwoSum pairs */
 } gbscan_f32_mode;
 
-typedef enum { GBSCAN_I32 = 0, GBSCAN_I64 = 1, GBSCAN_F32 = 2, GBSCAN_F64 = 3 } gbscan_dtype;
+typedef enum {
+    GBSCAN_I32 = 0,
+    GBSCAN_I64 = 1,
+    GBSCAN_F32 = 2,
+    GBSCAN_F64 = 3,
+    GBSCAN_U32 = 4  /* sums share the int32 kernels (the same bits); max / min compare unsigned */
+} gbscan_dtype;
 
 typedef enum {
-    GBSCAN_KIND_SCAN = 0,      /* one array, single-pass or two-pass */
-    GBSCAN_KIND_SEGMENTED = 1, /* CSR segments, one persistent launch */
-    GBSCAN_KIND_ROWS = 2,      /* rows x cols, along the last dim, forward or reverse */
-    GBSCAN_KIND_SCAN_MAX = 3,  /* one array, running maximum (int32, fp32) */
-    GBSCAN_KIND_SCAN_MIN = 4,  /* one array, running minimum (int32, fp32) */
-    GBSCAN_KIND_COMPACT = 5    /* stream compaction (int32, fp32) */
+    GBSCAN_KIND_SCAN = 0,           /* one array: single-pass, two-pass or partitioned */
+    GBSCAN_KIND_SEGMENTED = 1,      /* CSR segments, one persistent launch */
+    GBSCAN_KIND_ROWS = 2,           /* rows x cols, along the last dim, forward or reverse */
+    GBSCAN_KIND_SCAN_MAX = 3,       /* one array, running maximum (int32, int64, uint32, fp32) */
+    GBSCAN_KIND_SCAN_MIN = 4,       /* one array, running minimum (int32, int64, uint32, fp32) */
+    GBSCAN_KIND_COMPACT = 5,        /* stream compaction (int32, fp32) */
+    GBSCAN_KIND_SEGMENTED_MAX = 6,  /* CSR segments, running maximum (int32, fp32) */
+    GBSCAN_KIND_SEGMENTED_MIN = 7   /* CSR segments, running minimum (int32, fp32) */
 } gbscan_kind;
 
 /* Bytes of workspace needed by any call of `kind` on `dtype` with n elements
@@ -129,6 +137,14 @@ gbscan_status scan_inclusive_f32(const float* in, float* out, int64_t n, gbscan_
                                  cudaStream_t stream);
 gbscan_status scan_exclusive_f32(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
                                  void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+/* uint32 sums: modulo 2^32, the bits of the int32 sums of the same bits (they
+ * run the int32 kernels); workspace and variants as for GBSCAN_I32. */
+gbscan_status scan_inclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, void* ws,
+                                 size_t ws_bytes, gbscan_algo algo, int variant,
+                                 cudaStream_t stream);
+gbscan_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, void* ws,
+                                 size_t ws_bytes, gbscan_algo algo, int variant,
                                  cudaStream_t stream);
 /* fp64 scans: used by the autograd layer for double-precision gradient checks. */
 gbscan_status scan_inclusive_f64(const double* in, double* out, int64_t n, void* ws,
@@ -195,13 +211,14 @@ gbscan_status scan_get_device_status(void* ws, cudaStream_t stream);
  *   GBSCAN_OP_SUM  y_k = a_0 + ... + a_k    (the plain scans above)
  *   GBSCAN_OP_MAX  y_k = max(a_0, ..., a_k) (running maximum)
  *   GBSCAN_OP_MIN  y_k = min(a_0, ..., a_k) (running minimum)
- * Exclusive scans start from the operator's identity (0; INT32_MIN or -inf for
- * MAX; INT32_MAX or +inf for MIN).  fp32 MAX / MIN follow IEEE maxNum / minNum
- * (a NaN operand yields the other operand).  Arguments, workspace
- * (gbscan_workspace_size with GBSCAN_KIND_SCAN or the operator's kind),
- * algorithms and errors as for the plain scans; variants per
- * gbscan_num_variants(dtype, GBSCAN_KIND_SCAN_MAX / _MIN).  An unknown op
- * returns GBSCAN_ERR_INVALID_ARG.
+ * Exclusive scans start from the operator's identity (0 for SUM; INT32_MIN,
+ * INT64_MIN, 0 or -inf for MAX; INT32_MAX, INT64_MAX, UINT32_MAX or +inf for
+ * MIN, for int32, int64, uint32, fp32).  uint32 MAX / MIN compare unsigned.
+ * fp32 MAX / MIN follow IEEE maxNum / minNum (a NaN operand yields the other
+ * operand).  Arguments, workspace (gbscan_workspace_size with
+ * GBSCAN_KIND_SCAN or the operator's kind), algorithms and errors as for the
+ * plain scans; variants per gbscan_num_variants(dtype, GBSCAN_KIND_SCAN_MAX /
+ * _MIN).  An unknown op returns GBSCAN_ERR_INVALID_ARG.
  */
 typedef enum { GBSCAN_OP_SUM = 0, GBSCAN_OP_MAX = 1, GBSCAN_OP_MIN = 2 } gbscan_op;
 
@@ -211,6 +228,30 @@ gbscan_status scan_op_i32(const int32_t* in, int32_t* out, int64_t n, gbscan_op 
 gbscan_status scan_op_f32(const float* in, float* out, int64_t n, gbscan_op op, int exclusive,
                           void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                           cudaStream_t stream);
+gbscan_status scan_op_i64(const int64_t* in, int64_t* out, int64_t n, gbscan_op op,
+                          int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo,
+                          int variant, cudaStream_t stream);
+gbscan_status scan_op_u32(const uint32_t* in, uint32_t* out, int64_t n, gbscan_op op,
+                          int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo,
+                          int variant, cudaStream_t stream);
+
+/*
+ * Batched segmented scans under an operator: GBSCAN_OP_SUM is
+ * scan_segmented_batched_*; MAX and MIN give each segment's running maximum
+ * or minimum, an exclusive scan starting every segment from the operator's
+ * identity.  Arguments and errors as for scan_segmented_batched_*; workspace
+ * gbscan_workspace_size(dtype, GBSCAN_KIND_SEGMENTED_MAX / _MIN, n,
+ * num_segments); variants per that kind.  An unknown op returns
+ * GBSCAN_ERR_INVALID_ARG.
+ */
+gbscan_status scan_segmented_op_i32(const int32_t* in, int32_t* out, int64_t n,
+                                    const int64_t* offsets, int64_t num_segments, gbscan_op op,
+                                    int exclusive, void* ws, size_t ws_bytes, int variant,
+                                    cudaStream_t stream);
+gbscan_status scan_segmented_op_f32(const float* in, float* out, int64_t n,
+                                    const int64_t* offsets, int64_t num_segments, gbscan_op op,
+                                    int exclusive, void* ws, size_t ws_bytes, int variant,
+                                    cudaStream_t stream);
 
 /*
  * Stream compaction, an application of the exclusive scan (Section 1 names

@@ -62,6 +62,15 @@ def _declare(lib):
         "oracle_scan_min_i32": [vp, vp, i64, ci],
         "oracle_scan_max_f32": [vp, vp, i64, ci],
         "oracle_scan_min_f32": [vp, vp, i64, ci],
+        "oracle_scan_max_i64": [vp, vp, i64, ci],
+        "oracle_scan_min_i64": [vp, vp, i64, ci],
+        "oracle_scan_max_u32": [vp, vp, i64, ci],
+        "oracle_scan_min_u32": [vp, vp, i64, ci],
+        "oracle_scan_u32": [vp, vp, i64, ci],
+        "oracle_seg_scan_max_i32": [vp, vp, vp, i64, ci],
+        "oracle_seg_scan_min_i32": [vp, vp, vp, i64, ci],
+        "oracle_seg_scan_max_f32": [vp, vp, vp, i64, ci],
+        "oracle_seg_scan_min_f32": [vp, vp, vp, i64, ci],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -112,15 +121,24 @@ def scan_i64(a, exclusive: bool = False, lib=None) -> np.ndarray:
     return y
 
 
+def scan_u32(a, exclusive: bool = False, lib=None) -> np.ndarray:
+    a = _c(a, np.uint32)
+    y = np.empty_like(a)
+    (lib or _load()).oracle_scan_u32(a.ctypes.data, y.ctypes.data, a.size, int(exclusive))
+    return y
+
+
+_OP_KINDS = {np.dtype(np.int32): "i32", np.dtype(np.float32): "f32",
+             np.dtype(np.int64): "i64", np.dtype(np.uint32): "u32"}
+
+
 def scan_op(a, op: str, exclusive: bool = False, lib=None) -> np.ndarray:
-    """Running maximum or minimum (op "max" / "min") of int32 or float32 input."""
+    """Running maximum or minimum (op "max" / "min") of int32, int64, uint32 or
+    float32 input."""
     a = np.asarray(a)
-    if a.dtype == np.int32:
-        kind = "i32"
-    elif a.dtype == np.float32:
-        kind = "f32"
-    else:
-        raise TypeError("max / min scans take int32 or float32")
+    kind = _OP_KINDS.get(a.dtype)
+    if kind is None or op not in ("max", "min"):
+        raise TypeError("max / min scans take int32, int64, uint32 or float32")
     a = np.ascontiguousarray(a)
     y = np.empty_like(a)
     getattr(lib or _load(), f"oracle_scan_{op}_{kind}")(a.ctypes.data, y.ctypes.data, a.size,
@@ -205,6 +223,23 @@ def seg_scan_i64(a, offsets, exclusive: bool = False, lib=None) -> np.ndarray:
     y = np.zeros_like(a)
     (lib or _load()).oracle_seg_scan_i64(a.ctypes.data, y.ctypes.data, off.ctypes.data,
                                          off.size - 1, int(exclusive))
+    return y
+
+
+def seg_scan_op(a, offsets, op: str, exclusive: bool = False, lib=None) -> np.ndarray:
+    """Segmented running maximum or minimum of int32 or float32 input: each
+    segment on its own, an exclusive one starting from the operator's
+    identity; elements outside the segments stay 0."""
+    a = np.asarray(a)
+    kind = {np.dtype(np.int32): "i32", np.dtype(np.float32): "f32"}.get(a.dtype)
+    if kind is None or op not in ("max", "min"):
+        raise TypeError("segmented max / min scans take int32 or float32")
+    a = np.ascontiguousarray(a)
+    off = _check_offsets(offsets, a.size)
+    y = np.zeros_like(a)
+    getattr(lib or _load(), f"oracle_seg_scan_{op}_{kind}")(a.ctypes.data, y.ctypes.data,
+                                                             off.ctypes.data, off.size - 1,
+                                                             int(exclusive))
     return y
 
 

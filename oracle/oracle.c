@@ -9,8 +9,8 @@
  * for obviousness, not speed: one loop carrying a running total, exactly as the
  * paper states the problem (Section 1, Introduction: an inclusive scan outputs
  * [a0, a0+a1, ..., a0+...+a_{n-1}]; an exclusive scan drops the last of those
- * and puts the identity, 0, first; the basic algorithm is "one sequential pass
- * of additions ... writing out the running totals").
+ * and puts the identity, 0, first; the baseline algorithm walks the input
+ * once, adding each element to a running total and writing the total out).
  *
  * Readings where the paper is silent:
  *  - Integer overflow (the paper only uses fp32, Section 4.1): two's-complement
@@ -29,9 +29,15 @@
  *  - Other associative operators (Section 1 defines the scan for +; the same
  *    definition holds for any associative operator): the running maximum and
  *    minimum.  An exclusive scan starts from the operator's identity
- *    (INT32_MIN / -inf for max, INT32_MAX / +inf for min).  fp32 max and min
- *    are C's fmaxf / fminf (IEEE maxNum / minNum: a NaN operand yields the
- *    other one).
+ *    (INT32_MIN / INT64_MIN / 0 / -inf for max, INT32_MAX / INT64_MAX /
+ *    UINT32_MAX / +inf for min, for int32 / int64 / uint32 / fp32).  fp32 max
+ *    and min are C's fmaxf / fminf (IEEE maxNum / minNum: a NaN operand yields
+ *    the other one).  Segmented maxima and minima restart at every segment
+ *    start, like the segmented sums.
+ *  - Unsigned 32-bit sums: the same modular running total as int32 (the
+ *    bits of an int32 and a uint32 sum are the same); it has its own loop so
+ *    that the unsigned entry points are checked against an unsigned
+ *    definition.
  *  - Stream compaction (an application of the scan that Section 1 lists):
  *    copy, in order, the elements whose keep flag is nonzero; the number kept
  *    is the total of the flags.  Elements are moved as 4-byte words.
@@ -286,6 +292,91 @@ void oracle_scan_min_f32(const float* a, float* y, int64_t n, int exclusive) {
         if (exclusive) y[k] = run;
         run = fminf(run, a[k]);
         if (!exclusive) y[k] = run;
+    }
+}
+
+void oracle_scan_max_i64(const int64_t* a, int64_t* y, int64_t n, int exclusive) {
+    int64_t run = INT64_MIN;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) y[k] = run;
+        if (a[k] > run) run = a[k];
+        if (!exclusive) y[k] = run;
+    }
+}
+
+void oracle_scan_min_i64(const int64_t* a, int64_t* y, int64_t n, int exclusive) {
+    int64_t run = INT64_MAX;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) y[k] = run;
+        if (a[k] < run) run = a[k];
+        if (!exclusive) y[k] = run;
+    }
+}
+
+void oracle_scan_max_u32(const uint32_t* a, uint32_t* y, int64_t n, int exclusive) {
+    uint32_t run = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) y[k] = run;
+        if (a[k] > run) run = a[k];
+        if (!exclusive) y[k] = run;
+    }
+}
+
+void oracle_scan_min_u32(const uint32_t* a, uint32_t* y, int64_t n, int exclusive) {
+    uint32_t run = UINT32_MAX;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) y[k] = run;
+        if (a[k] < run) run = a[k];
+        if (!exclusive) y[k] = run;
+    }
+}
+
+/* ---- unsigned 32-bit sums ------------------------------------------------ */
+
+void oracle_scan_u32(const uint32_t* a, uint32_t* y, int64_t n, int exclusive) {
+    uint32_t run = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        if (exclusive) {
+            y[k] = run;
+            run += a[k];
+        } else {
+            run += a[k];
+            y[k] = run;
+        }
+    }
+}
+
+/* ---- segmented running maximum / minimum --------------------------------- */
+
+void oracle_seg_scan_max_i32(const int32_t* a, int32_t* y, const int64_t* offsets,
+                             int64_t num_segments, int exclusive) {
+    for (int64_t s = 0; s < num_segments; ++s) {
+        int64_t b = offsets[s], e = offsets[s + 1];
+        if (e > b) oracle_scan_max_i32(a + b, y + b, e - b, exclusive);
+    }
+}
+
+void oracle_seg_scan_min_i32(const int32_t* a, int32_t* y, const int64_t* offsets,
+                             int64_t num_segments, int exclusive) {
+    for (int64_t s = 0; s < num_segments; ++s) {
+        int64_t b = offsets[s], e = offsets[s + 1];
+        if (e > b) oracle_scan_min_i32(a + b, y + b, e - b, exclusive);
+    }
+}
+
+void oracle_seg_scan_max_f32(const float* a, float* y, const int64_t* offsets,
+                             int64_t num_segments, int exclusive) {
+    for (int64_t s = 0; s < num_segments; ++s) {
+        int64_t b = offsets[s], e = offsets[s + 1];
+        if (e > b) oracle_scan_max_f32(a + b, y + b, e - b, exclusive);
+    }
+}
+
+void oracle_seg_scan_min_f32(const float* a, float* y, const int64_t* offsets,
+                             int64_t num_segments, int exclusive) {
+    for (int64_t s = 0; s < num_segments; ++s) {
+        int64_t b = offsets[s], e = offsets[s + 1];
+        if (e > b) oracle_scan_min_f32(a + b, y + b, e - b, exclusive);
     }
 }
 

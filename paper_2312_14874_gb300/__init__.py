@@ -10,11 +10,11 @@ points on the current torch stream.  There is no CPU fallback: a CPU tensor is
 rejected.
 
 Public API:
-    inclusive(x), exclusive(x), scan(x, exclusive=...)  1-D int32/int64/float32/float64
-    scan(x, op="max" | "min")                           running max / min, int32/float32
+    inclusive(x), exclusive(x), scan(x, exclusive=...)  int32/int64/uint32/float32/float64
+    scan(x, op="max" | "min")                           running max / min, int32/int64/uint32/float32
     compact(x, flags)                                    stream compaction, int32/float32
     inclusive_host(h_in)                                 int32 scan of a host array, pipelined
-    segmented(x, offsets, exclusive=...)                  CSR segments, int32/float32
+    segmented(x, offsets, exclusive=..., op=...)          CSR segments, int32/float32, sum/max/min
     rows(x, exclusive=...), backward(g, exclusive=...)    along the last dim, float32/float64
     cumsum(x, dim=-1, exclusive=False)                    differentiable (autograd)
     device_status(), copy_(dst, src), Workspace
@@ -39,6 +39,7 @@ _DTYPES = {
     torch.int64: (_capi.I64, "i64"),
     torch.float32: (_capi.F32, "f32"),
     torch.float64: (_capi.F64, "f64"),
+    torch.uint32: (_capi.U32, "u32"),
 }
 _ALGOS = {"auto": _capi.ALGO_AUTO, "single_pass": _capi.ALGO_SINGLE_PASS,
           "two_pass": _capi.ALGO_TWO_PASS, "partitioned": _capi.ALGO_PARTITIONED}
@@ -133,22 +134,28 @@ def scan(x: torch.Tensor, exclusive: bool = False, *, out: torch.Tensor | None =
     if op not in _OPS:
         raise ValueError(f"unknown op {op!r}")
     if op != "sum":
-        if x.dtype not in (torch.int32, torch.float32) or compensated:
-            raise TypeError("max / min scans take int32 or float32 (no compensation)")
+        if x.dtype not in (torch.int32, torch.int64, torch.uint32, torch.float32) or compensated:
+            raise TypeError("max / min scans take int32, int64, uint32 or float32 (no compensation)")
         if algo not in _ALGOS:
             raise ValueError(f"unknown algo {algo!r}")
         v = 0 if variant is None else int(variant)
         ws = workspace or _workspace_for(x.device, workspace_bytes(x.dtype, _capi.KIND_SCAN, n))
-        fn = _capi.lib().scan_op_i32 if key == "i32" else _capi.lib().scan_op_f32
+        fn = getattr(_capi.lib(), f"scan_op_{key}")
         _capi.check(fn(x.data_ptr(), out.data_ptr(), n, _OPS[op], int(exclusive), ws.ptr, ws.nbytes,
                        _ALGOS[algo], v, _stream_handle(x.device)), "scan_op")
         return out
-    kind_key = "scan_" + key + ("c" if compensated else "")
+    if key == "u32":
+        # uint32 sums are the int32 sums of the same bits (modulo 2^32): the
+        # int32 tuning applies
+        key_tune = "i32"
+    else:
+        key_tune = key
+    kind_key = "scan_" + key_tune + ("c" if compensated else "")
     if algo not in _ALGOS:
         raise ValueError(f"unknown algo {algo!r}")
     if variant is None:
         from . import autotune
-        algo, v = autotune.choose(kind_key, key, n, algo)
+        algo, v = autotune.choose(kind_key, key_tune, n, algo)
     else:
         v = int(variant)
     ws = workspace or _workspace_for(x.device, workspace_bytes(x.dtype, _capi.KIND_SCAN, n))
@@ -241,10 +248,12 @@ def compact(x: torch.Tensor, flags: torch.Tensor, *, out: torch.Tensor | None = 
 
 def segmented(x: torch.Tensor, offsets: torch.Tensor, exclusive: bool = False, *,
               out: torch.Tensor | None = None, variant: int | None = None,
-              workspace: Workspace | None = None) -> torch.Tensor:
+              workspace: Workspace | None = None, op: str = "sum") -> torch.Tensor:
     """Scan of every segment [offsets[s], offsets[s+1]) of a flat tensor, in one
     persistent launch.  ``offsets`` is an int64 CUDA tensor of S+1 entries from 0
-    to x.numel().  Malformed offsets are reported by device_status()."""
+    to x.numel().  ``op`` "max" / "min" gives each segment's running maximum /
+    minimum (an exclusive one starts every segment from the operator's
+    identity).  Malformed offsets are reported by device_status()."""
     _check_cuda(x, "x")
     _check_cuda(offsets, "offsets")
     if x.dtype not in (torch.int32, torch.float32):
@@ -262,12 +271,22 @@ def segmented(x: torch.Tensor, offsets: torch.Tensor, exclusive: bool = False, *
         return out
     if nseg < 1:
         raise ValueError("offsets needs at least two entries")
-    v = _variant("seg_" + key, key, n, variant)
-    ws = workspace or _workspace_for(
-        x.device, workspace_bytes(x.dtype, _capi.KIND_SEGMENTED, n, nseg))
-    fn = getattr(_capi.lib(), f"scan_segmented_batched_{key}")
-    _capi.check(fn(x.data_ptr(), out.data_ptr(), n, offsets.data_ptr(), nseg, int(exclusive),
-                   ws.ptr, ws.nbytes, v, _stream_handle(x.device)), "segmented")
+    if op not in _OPS:
+        raise ValueError(f"unknown op {op!r}")
+    if op == "sum":
+        v = _variant("seg_" + key, key, n, variant)
+        ws = workspace or _workspace_for(
+            x.device, workspace_bytes(x.dtype, _capi.KIND_SEGMENTED, n, nseg))
+        fn = getattr(_capi.lib(), f"scan_segmented_batched_{key}")
+        _capi.check(fn(x.data_ptr(), out.data_ptr(), n, offsets.data_ptr(), nseg, int(exclusive),
+                       ws.ptr, ws.nbytes, v, _stream_handle(x.device)), "segmented")
+        return out
+    v = 0 if variant is None else int(variant)
+    kind = _capi.KIND_SEGMENTED_MAX if op == "max" else _capi.KIND_SEGMENTED_MIN
+    ws = workspace or _workspace_for(x.device, workspace_bytes(x.dtype, kind, n, nseg))
+    fn = getattr(_capi.lib(), f"scan_segmented_op_{key}")
+    _capi.check(fn(x.data_ptr(), out.data_ptr(), n, offsets.data_ptr(), nseg, _OPS[op],
+                   int(exclusive), ws.ptr, ws.nbytes, v, _stream_handle(x.device)), "segmented_op")
     return out
 
 

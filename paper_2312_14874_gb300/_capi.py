@@ -28,9 +28,10 @@ ALGO_AUTO, ALGO_SINGLE_PASS, ALGO_TWO_PASS, ALGO_PARTITIONED = 0, 1, 2, 3
 # gbscan_f32_mode
 F32_PLAIN, F32_COMPENSATED = 0, 1
 # gbscan_dtype
-I32, I64, F32, F64 = 0, 1, 2, 3
+I32, I64, F32, F64, U32 = 0, 1, 2, 3, 4
 # gbscan_kind
 KIND_SCAN, KIND_SEGMENTED, KIND_ROWS, KIND_SCAN_MAX, KIND_SCAN_MIN, KIND_COMPACT = 0, 1, 2, 3, 4, 5
+KIND_SEGMENTED_MAX, KIND_SEGMENTED_MIN = 6, 7
 # gbscan_op
 OP_SUM, OP_MAX, OP_MIN = 0, 1, 2
 
@@ -65,6 +66,12 @@ _SIGNATURES = {
     "scan_inclusive_i32_noalloc": [_vp, _vp, _i64, _vp],
     "scan_op_i32": [_vp, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _i32, _vp],
     "scan_op_f32": [_vp, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _i32, _vp],
+    "scan_op_i64": [_vp, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _i32, _vp],
+    "scan_op_u32": [_vp, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _i32, _vp],
+    "scan_inclusive_u32": [_vp, _vp, _i64, _vp, _sz, _i32, _i32, _vp],
+    "scan_exclusive_u32": [_vp, _vp, _i64, _vp, _sz, _i32, _i32, _vp],
+    "scan_segmented_op_i32": [_vp, _vp, _i64, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _vp],
+    "scan_segmented_op_f32": [_vp, _vp, _i64, _vp, _i64, _i32, _i32, _vp, _sz, _i32, _vp],
     "compact_i32": [_vp, _vp, _vp, _i64, _vp, _vp, _sz, _i32, _vp],
     "compact_f32": [_vp, _vp, _vp, _i64, _vp, _vp, _sz, _i32, _vp],
     "scan_inclusive_i32_host": [_vp, _vp, _i64, _vp, _i64, _vp, _sz, _vp],

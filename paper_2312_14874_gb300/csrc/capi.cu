@@ -144,7 +144,7 @@ int min_tile(gbscan_dtype dt) {
     return (dt == GBSCAN_I64 || dt == GBSCAN_F64) ? kMinTile8 : kMinTile4;
 }
 
-bool valid_dtype(int dt) { return dt >= GBSCAN_I32 && dt <= GBSCAN_F64; }
+bool valid_dtype(int dt) { return dt >= GBSCAN_I32 && dt <= GBSCAN_U32; }
 
 // Records needed for n elements at tile size `tile`: one per tile plus the
 // segment locator's end sentinel; they come in blocks of 16.
@@ -398,6 +398,7 @@ const Family* family_for(gbscan_dtype dt, gbscan_kind kind) {
     case GBSCAN_KIND_SCAN:
         switch (dt) {
         case GBSCAN_I32: return &family_scan_i32();
+        case GBSCAN_U32: return &family_scan_i32();  // sums: the same bits
         case GBSCAN_I64: return &family_scan_i64();
         case GBSCAN_F32: return &family_scan_f32();
         case GBSCAN_F64: return &family_scan_f64();
@@ -414,13 +415,25 @@ const Family* family_for(gbscan_dtype dt, gbscan_kind kind) {
     case GBSCAN_KIND_SCAN_MAX:
         if (dt == GBSCAN_I32) return &family_max_i32();
         if (dt == GBSCAN_F32) return &family_max_f32();
+        if (dt == GBSCAN_I64) return &family_max_i64();
+        if (dt == GBSCAN_U32) return &family_max_u32();
         break;
     case GBSCAN_KIND_SCAN_MIN:
         if (dt == GBSCAN_I32) return &family_min_i32();
         if (dt == GBSCAN_F32) return &family_min_f32();
+        if (dt == GBSCAN_I64) return &family_min_i64();
+        if (dt == GBSCAN_U32) return &family_min_u32();
         break;
     case GBSCAN_KIND_COMPACT:
         if (dt == GBSCAN_I32 || dt == GBSCAN_F32) return &family_compact();
+        break;
+    case GBSCAN_KIND_SEGMENTED_MAX:
+        if (dt == GBSCAN_I32) return &family_seg_max_i32();
+        if (dt == GBSCAN_F32) return &family_seg_max_f32();
+        break;
+    case GBSCAN_KIND_SEGMENTED_MIN:
+        if (dt == GBSCAN_I32) return &family_seg_min_i32();
+        if (dt == GBSCAN_F32) return &family_seg_min_f32();
         break;
     }
     return nullptr;
@@ -442,12 +455,14 @@ gbscan_status gbscan_workspace_size(gbscan_dtype dtype, gbscan_kind kind, int64_
                                     int64_t num_segments, size_t* bytes) {
     if (bytes == nullptr || n < 0 || num_segments < 0 || !valid_dtype(dtype))
         return GBSCAN_ERR_INVALID_ARG;
-    if (kind < GBSCAN_KIND_SCAN || kind > GBSCAN_KIND_COMPACT) return GBSCAN_ERR_INVALID_ARG;
+    if (kind < GBSCAN_KIND_SCAN || kind > GBSCAN_KIND_SEGMENTED_MIN) return GBSCAN_ERR_INVALID_ARG;
     if (num_segments > INT32_MAX) return GBSCAN_ERR_UNSUPPORTED;
     const int tile = min_tile(dtype);
     if ((n + tile - 1) / tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
     *bytes = kHeaderBytes + record_bytes(records_for(n, tile));
-    if (kind == GBSCAN_KIND_SEGMENTED) *bytes += seg_bitmap_bytes(n);
+    if (kind == GBSCAN_KIND_SEGMENTED || kind == GBSCAN_KIND_SEGMENTED_MAX ||
+        kind == GBSCAN_KIND_SEGMENTED_MIN)
+        *bytes += seg_bitmap_bytes(n);
     return GBSCAN_OK;
 }
 
@@ -469,6 +484,8 @@ GBSCAN_FLAT(scan_inclusive_i32, int32_t, family_scan_i32, 0)
 GBSCAN_FLAT(scan_exclusive_i32, int32_t, family_scan_i32, 1)
 GBSCAN_FLAT(scan_inclusive_i64, int64_t, family_scan_i64, 0)
 GBSCAN_FLAT(scan_exclusive_i64, int64_t, family_scan_i64, 1)
+GBSCAN_FLAT(scan_inclusive_u32, uint32_t, family_scan_i32, 0)
+GBSCAN_FLAT(scan_exclusive_u32, uint32_t, family_scan_i32, 1)
 GBSCAN_FLAT(scan_inclusive_f64, double, family_scan_f64, 0)
 GBSCAN_FLAT(scan_exclusive_f64, double, family_scan_f64, 1)
 
@@ -622,6 +639,60 @@ gbscan_status scan_op_f32(const float* in, float* out, int64_t n, gbscan_op op, 
     if (!fam) return GBSCAN_ERR_INVALID_ARG;
     return scan_flat(*fam, in, out, n, sizeof(float), exclusive != 0, ws, ws_bytes, algo, variant,
                      stream);
+}
+
+gbscan_status scan_op_i64(const int64_t* in, int64_t* out, int64_t n, gbscan_op op,
+                          int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo,
+                          int variant, cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_op_i64");
+    const Family* fam = op == GBSCAN_OP_SUM ? &family_scan_i64()
+                        : op == GBSCAN_OP_MAX ? &family_max_i64()
+                        : op == GBSCAN_OP_MIN ? &family_min_i64()
+                                              : nullptr;
+    if (!fam) return GBSCAN_ERR_INVALID_ARG;
+    return scan_flat(*fam, in, out, n, sizeof(int64_t), exclusive != 0, ws, ws_bytes, algo,
+                     variant, stream);
+}
+
+gbscan_status scan_op_u32(const uint32_t* in, uint32_t* out, int64_t n, gbscan_op op,
+                          int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo,
+                          int variant, cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_op_u32");
+    const Family* fam = op == GBSCAN_OP_SUM ? &family_scan_i32()
+                        : op == GBSCAN_OP_MAX ? &family_max_u32()
+                        : op == GBSCAN_OP_MIN ? &family_min_u32()
+                                              : nullptr;
+    if (!fam) return GBSCAN_ERR_INVALID_ARG;
+    return scan_flat(*fam, in, out, n, sizeof(uint32_t), exclusive != 0, ws, ws_bytes, algo,
+                     variant, stream);
+}
+
+gbscan_status scan_segmented_op_i32(const int32_t* in, int32_t* out, int64_t n,
+                                    const int64_t* offsets, int64_t num_segments, gbscan_op op,
+                                    int exclusive, void* ws, size_t ws_bytes, int variant,
+                                    cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_segmented_op_i32");
+    const Family* fam = op == GBSCAN_OP_SUM ? &family_seg_i32()
+                        : op == GBSCAN_OP_MAX ? &family_seg_max_i32()
+                        : op == GBSCAN_OP_MIN ? &family_seg_min_i32()
+                                              : nullptr;
+    if (!fam) return GBSCAN_ERR_INVALID_ARG;
+    return scan_seg_impl(*fam, in, out, n, offsets, num_segments, sizeof(int32_t), exclusive != 0,
+                         ws, ws_bytes, variant, stream);
+}
+
+gbscan_status scan_segmented_op_f32(const float* in, float* out, int64_t n,
+                                    const int64_t* offsets, int64_t num_segments, gbscan_op op,
+                                    int exclusive, void* ws, size_t ws_bytes, int variant,
+                                    cudaStream_t stream) {
+    GBSCAN_NVTX_RANGE("scan_segmented_op_f32");
+    const Family* fam = op == GBSCAN_OP_SUM ? &family_seg_f32()
+                        : op == GBSCAN_OP_MAX ? &family_seg_max_f32()
+                        : op == GBSCAN_OP_MIN ? &family_seg_min_f32()
+                                              : nullptr;
+    if (!fam) return GBSCAN_ERR_INVALID_ARG;
+    return scan_seg_impl(*fam, in, out, n, offsets, num_segments, sizeof(float), exclusive != 0,
+                         ws, ws_bytes, variant, stream);
 }
 
 gbscan_status scan_segmented_batched_i32(const int32_t* in, int32_t* out, int64_t n,

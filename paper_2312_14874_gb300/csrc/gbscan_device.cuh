@@ -519,6 +519,76 @@ struct OpMinF32 {
     __device__ static Acc from_bits(Bits b) { return __uint_as_float(b); }
 };
 
+// Running maximum and minimum of int64 (identities INT64_MIN / INT64_MAX) and
+// of uint32 (unsigned order; identities 0 / UINT32_MAX).
+struct OpMaxI64 {
+    using T = int64_t;
+    using Acc = long long;
+    using Bits = unsigned long long;
+    static constexpr bool kPacked = false;
+    static constexpr int kSplit = 1;  // independent chains a thread sums its items in
+    __device__ static T pad() { return INT64_MIN; }
+    __device__ static Acc identity() { return INT64_MIN; }
+    __device__ static Acc lift(T x) { return x; }
+    __device__ static Acc combine(Acc a, Acc b) { return a > b ? a : b; }
+    __device__ static void accumulate(Acc& r, T x) { r = r > x ? r : x; }
+    __device__ static T output(Acc c, Acc l) { return c > l ? c : l; }
+    __device__ static T output1(Acc v) { return v; }
+    __device__ static Bits to_bits(Acc a) { return static_cast<Bits>(a); }
+    __device__ static Acc from_bits(Bits b) { return static_cast<Acc>(b); }
+};
+
+struct OpMinI64 {
+    using T = int64_t;
+    using Acc = long long;
+    using Bits = unsigned long long;
+    static constexpr bool kPacked = false;
+    static constexpr int kSplit = 1;  // independent chains a thread sums its items in
+    __device__ static T pad() { return INT64_MAX; }
+    __device__ static Acc identity() { return INT64_MAX; }
+    __device__ static Acc lift(T x) { return x; }
+    __device__ static Acc combine(Acc a, Acc b) { return a < b ? a : b; }
+    __device__ static void accumulate(Acc& r, T x) { r = r < x ? r : x; }
+    __device__ static T output(Acc c, Acc l) { return c < l ? c : l; }
+    __device__ static T output1(Acc v) { return v; }
+    __device__ static Bits to_bits(Acc a) { return static_cast<Bits>(a); }
+    __device__ static Acc from_bits(Bits b) { return static_cast<Acc>(b); }
+};
+
+struct OpMaxU32 {
+    using T = uint32_t;
+    using Acc = uint32_t;
+    using Bits = uint32_t;
+    static constexpr bool kPacked = true;
+    static constexpr int kSplit = 1;  // independent chains a thread sums its items in
+    __device__ static T pad() { return 0u; }
+    __device__ static Acc identity() { return 0u; }
+    __device__ static Acc lift(T x) { return x; }
+    __device__ static Acc combine(Acc a, Acc b) { return a > b ? a : b; }
+    __device__ static void accumulate(Acc& r, T x) { r = r > x ? r : x; }
+    __device__ static T output(Acc c, Acc l) { return c > l ? c : l; }
+    __device__ static T output1(Acc v) { return v; }
+    __device__ static Bits to_bits(Acc a) { return a; }
+    __device__ static Acc from_bits(Bits b) { return b; }
+};
+
+struct OpMinU32 {
+    using T = uint32_t;
+    using Acc = uint32_t;
+    using Bits = uint32_t;
+    static constexpr bool kPacked = true;
+    static constexpr int kSplit = 1;  // independent chains a thread sums its items in
+    __device__ static T pad() { return 0xffffffffu; }
+    __device__ static Acc identity() { return 0xffffffffu; }
+    __device__ static Acc lift(T x) { return x; }
+    __device__ static Acc combine(Acc a, Acc b) { return a < b ? a : b; }
+    __device__ static void accumulate(Acc& r, T x) { r = r < x ? r : x; }
+    __device__ static T output(Acc c, Acc l) { return c < l ? c : l; }
+    __device__ static T output1(Acc v) { return v; }
+    __device__ static Bits to_bits(Acc a) { return a; }
+    __device__ static Acc from_bits(Bits b) { return b; }
+};
+
 // Compensated fp32.  Every carry is an unevaluated pair hi + lo combined with
 // Knuth's TwoSum and renormalised: the sub-block, thread, warp, block, tile and
 // chunk prefixes, so no error accumulates along the array beyond O(u^2) per

@@ -194,6 +194,14 @@ const Family& family_min_i32();
 const Family& family_max_f32();
 const Family& family_min_f32();
 const Family& family_compact();
+const Family& family_max_i64();
+const Family& family_min_i64();
+const Family& family_max_u32();
+const Family& family_min_u32();
+const Family& family_seg_max_i32();
+const Family& family_seg_min_i32();
+const Family& family_seg_max_f32();
+const Family& family_seg_min_f32();
 
 // Smallest tile (in elements) of any variant for an element size: sizes the
 // workspace so that every variant fits.

@@ -11,7 +11,10 @@ against the oracle.
   CUDA-graph path: int32 U[0, 3] bit-exact, fp32 U[0, 1) within 1e-5.
 - [4096, 8192] fp32 N(0, 1): the row scan and its backward (suffix scan)
   within 1e-5.
-- int32 n = 2^30 running maximum and minimum, every algorithm, bit-exact.
+- int32 n = 2^30 running maximum and minimum, every algorithm, bit-exact;
+  int64 n = 2^29 running maximum and minimum and uint32 n = 2^30 sums, every
+  algorithm, bit-exact; segmented maximum and minimum of the 65,536-segment
+  batch, bit-exact.
 - Stream compaction of int32 n = 2^30 with half the elements kept, bit-exact.
 
 The measured errors are printed; with GBSCAN_PARITY_REPORT set to a path they
@@ -108,6 +111,51 @@ def test_int64_2e29_every_algorithm():
         assert gb.device_status() == 0, algo
         assert np.array_equal(y.cpu().numpy(), want), algo
     record("i64_2^29_inclusive", "bit-exact: " + ", ".join(ALGOS))
+
+
+def test_uint32_2e30_sums():
+    """uint32 inclusive sums of 2^30 values spanning the whole range (the
+    total wraps many times), tuned variant of every algorithm, bit-exact."""
+    n = 1 << 30
+    a = synth.uniform_i64(n, 1 << 32, seed=3).astype(np.uint32)
+    want = oracle.scan_u32(a)
+    x = torch.from_numpy(a.view(np.int32)).to(dev()).view(torch.uint32)
+    y = torch.empty_like(x)
+    for algo in ALGOS:
+        y.view(torch.int32).fill_(-1)
+        gb.scan(x, out=y, algo=algo, variant=tuned("scan_i32", n, algo))
+        assert gb.device_status() == 0, algo
+        assert np.array_equal(y.view(torch.int32).cpu().numpy().view(np.uint32), want), algo
+    record("u32_2^30_inclusive", "bit-exact: " + ", ".join(ALGOS))
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_int64_2e29_running_max_min(op):
+    n = 1 << 29
+    a = synth.uniform_i64(n, 1 << 32, seed=4).astype(np.int64) * 2_000_003 - (1 << 52)
+    want = oracle.scan_op(a, op)
+    x = torch.from_numpy(a).to(dev())
+    y = torch.empty_like(x)
+    for algo in ALGOS:
+        y.fill_(0)
+        gb.scan(x, out=y, op=op, algo=algo, variant=2)
+        assert gb.device_status() == 0, algo
+        assert np.array_equal(y.cpu().numpy(), want), algo
+    record(f"i64_2^29_running_{op}", "bit-exact: " + ", ".join(ALGOS))
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_segmented_65536_max_min(op):
+    """Segmented running maximum / minimum of the 65,536-segment batch, int32,
+    exclusive, bit-exact."""
+    off = synth.segment_offsets(65536, max_log2=16, seed=0)
+    n = int(off[-1])
+    a = (synth.uniform_i32(n, 1 << 31, seed=5).astype(np.int64) - (1 << 30)).astype(np.int32)
+    want = oracle.seg_scan_op(a, off, op, True)
+    y = gb.segmented(torch.from_numpy(a).to(dev()), torch.from_numpy(off).to(dev()), True, op=op)
+    assert gb.device_status() == 0
+    assert np.array_equal(y.cpu().numpy(), want)
+    record(f"seg_i32_65536_exclusive_{op}", f"bit-exact, n = {n}")
 
 
 @pytest.mark.parametrize("dist", ["uniform", "normal"])

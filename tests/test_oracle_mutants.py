@@ -102,6 +102,37 @@ def pins_pass(lib) -> bool:
                         for k in range(arr.size)]
                 checks.append(np.array_equal(oracle.scan_op(arr, op, excl, lib=lib),
                                              np.array(want, dtype=arr.dtype)))
+    # int64 and uint32 running max / min (their own identities and, for
+    # uint32, unsigned order), against the same O(n^2) definition
+    r64 = synth.uniform_i64(40, 1 << 32, seed=9).astype(np.int64) * 256 - (1 << 39)
+    ru = (synth.uniform_i64(40, 1 << 32, seed=10)).astype(np.uint32)
+    for op, f in (("max", max), ("min", min)):
+        for excl in (False, True):
+            for arr, ident in ((r64, np.iinfo(np.int64).min if op == "max" else np.iinfo(np.int64).max),
+                               (ru, 0 if op == "max" else np.iinfo(np.uint32).max)):
+                want = [f(arr[: k if excl else k + 1].tolist()) if (k or not excl) else ident
+                        for k in range(arr.size)]
+                checks.append(np.array_equal(oracle.scan_op(arr, op, excl, lib=lib),
+                                             np.array(want, dtype=arr.dtype)))
+    # uint32 sums: the modular running total (numpy uint32 cumsum wraps)
+    for excl in (False, True):
+        want = np.cumsum(ru, dtype=np.uint64) % (1 << 32)
+        if excl:
+            want = np.concatenate([[0], want[:-1]])
+        checks.append(np.array_equal(oracle.scan_u32(ru, excl, lib=lib), want.astype(np.uint32)))
+    # segmented max / min: each segment on its own (empty segments included)
+    so = [0, 7, 7, 19, 40]
+    for op, f in (("max", max), ("min", min)):
+        for excl in (False, True):
+            for arr, ident in ((r, np.iinfo(np.int32).min if op == "max" else np.iinfo(np.int32).max),
+                               (rf, -np.inf if op == "max" else np.inf)):
+                want = []
+                for b, e in zip(so[:-1], so[1:]):
+                    seg = arr[b:e].tolist()
+                    want += [f(seg[: k if excl else k + 1]) if (k or not excl) else ident
+                             for k in range(e - b)]
+                checks.append(np.array_equal(oracle.seg_scan_op(arr, so, op, excl, lib=lib),
+                                             np.array(want, dtype=arr.dtype)))
     cf = (synth.uniform_i32(50, 2, seed=7)).astype(np.uint8)
     cv = synth.uniform_i32(50, 1000, seed=8)
     checks.append(np.array_equal(oracle.compact(cv, cf, lib=lib),
@@ -139,6 +170,16 @@ MUTANTS = {
     "compaction keeps the dropped": ("if (flags[i] != 0) out[j++] = in[i];", "if (flags[i] == 0) out[j++] = in[i];", 0),
     "compaction writes in place of the input index": ("if (flags[i] != 0) out[j++] = in[i];",
                                                       "if (flags[i] != 0) { out[j] = in[j]; j++; }", 0),
+    "i64 min starts from INT64_MIN": ("    int64_t run = INT64_MAX;", "    int64_t run = INT64_MIN;", 0),
+    "u32 max compares signed": ("        if (a[k] > run) run = a[k];\n        if (!exclusive) y[k] = run;\n    }\n}\n\nvoid oracle_scan_min_u32",
+                                "        if ((int32_t)a[k] > (int32_t)run) run = a[k];\n        if (!exclusive) y[k] = run;\n    }\n}\n\nvoid oracle_scan_min_u32", 0),
+    "u32 min starts from 0": ("    uint32_t run = UINT32_MAX;", "    uint32_t run = 0;", 0),
+    "u32 sum exclusive adds before writing": ("            y[k] = run;\n            run += a[k];",
+                                              "            run += a[k];\n            y[k] = run;", 0),
+    "segmented max does not restart": ("if (e > b) oracle_scan_max_i32(a + b, y + b, e - b, exclusive);",
+                                       "if (e > b) oracle_scan_max_i32(a + offsets[0], y + offsets[0], e - offsets[0], exclusive);", 0),
+    "segmented f32 min uses max": ("if (e > b) oracle_scan_min_f32(a + b, y + b, e - b, exclusive);",
+                                   "if (e > b) oracle_scan_max_f32(a + b, y + b, e - b, exclusive);", 0),
     "plain double exclusive shifted": ("y[k] = run;\n            run += (double)a[k];",
                                        "run += (double)a[k];\n            y[k] = run;", 0),
 }
