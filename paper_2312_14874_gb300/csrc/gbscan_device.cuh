@@ -493,7 +493,8 @@ struct OpMaxF32 {
     static constexpr int kSplit = 1;  // independent chains a thread sums its items in
     __device__ static T pad() { return -__int_as_float(0x7f800000); }
     __device__ static Acc identity() { return -__int_as_float(0x7f800000); }
-    __device__ static Acc lift(T x) { return x; }
+    // a run (or a segment) starts from the identity: a NaN first element is skipped
+    __device__ static Acc lift(T x) { return fmaxf(identity(), x); }
     __device__ static Acc combine(Acc a, Acc b) { return fmaxf(a, b); }
     __device__ static void accumulate(Acc& r, T x) { r = fmaxf(r, x); }
     __device__ static T output(Acc c, Acc l) { return fmaxf(c, l); }
@@ -510,7 +511,8 @@ struct OpMinF32 {
     static constexpr int kSplit = 1;  // independent chains a thread sums its items in
     __device__ static T pad() { return __int_as_float(0x7f800000); }
     __device__ static Acc identity() { return __int_as_float(0x7f800000); }
-    __device__ static Acc lift(T x) { return x; }
+    // a run (or a segment) starts from the identity: a NaN first element is skipped
+    __device__ static Acc lift(T x) { return fminf(identity(), x); }
     __device__ static Acc combine(Acc a, Acc b) { return fminf(a, b); }
     __device__ static void accumulate(Acc& r, T x) { r = fminf(r, x); }
     __device__ static T output(Acc c, Acc l) { return fminf(c, l); }

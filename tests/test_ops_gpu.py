@@ -179,6 +179,8 @@ def test_segmented_max_min(op, key):
         if n == 0:
             continue
         a = data(key, n, seed=seed)
+        if key == "f32":
+            a[off[:-1][off[:-1] < n][::3]] = np.nan  # NaN segment heads: skipped, as maxNum does
         x = torch.from_numpy(a).to(dev())
         o = torch.from_numpy(off).to(dev())
         for v in range(gb.num_variants(dt, kind)):
