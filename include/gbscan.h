@@ -113,9 +113,9 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
  *               environment variable GBSCAN_CHUNK_BYTES; each chunk is reduced tile by
  *               tile, its tile sums are scanned, and it is scanned a second time while
  *               still in L2, overlapped with the reduction of the chunk four ahead,
- *               GBSCAN_CHUNK_LAG), or AUTO (PARTITIONED for inputs of 128 MiB or
- *               more, TWO_PASS below and for compensated fp32 at any size: the
- *               fastest choice measured on GB300).
+ *               GBSCAN_CHUNK_LAG), or AUTO (4-byte elements: PARTITIONED for inputs of
+ *               128 MiB or more, SINGLE_PASS below; int64: SINGLE_PASS; compensated
+ *               fp32 and fp64: TWO_PASS; the fastest choices measured on GB300).
  *   variant   : launch shape (threads, items per thread, pipeline stages), 0 = default;
  *               see gbscan_num_variants / gbscan_variant_info.
  *   mode      : (f32 only) plain fp32 or compensated two-sum carries.

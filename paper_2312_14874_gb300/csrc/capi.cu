@@ -231,11 +231,12 @@ static long long env_cached(std::atomic<long long>& cache, const char* name, lon
     return v;
 }
 
-// GBSCAN_ALGO_AUTO takes the partitioned scan from this input size on and the
-// two-pass scan below it, where the data stays in L2 between the passes anyway
-// (measured on GB300: two-pass is the fastest up to 64 MiB, partitioned from
-// 256 MiB; compensated fp32, whose scan is bound by its TwoSum chains, is
-// fastest two-pass at every size).
+// GBSCAN_ALGO_AUTO: 4-byte elements take the partitioned scan from this input
+// size on and the single-pass scan (one launch) below it; 8-byte elements take
+// the single-pass scan at every size (measured on GB300: int64 single-pass is
+// the fastest from 2^24 to 2^30 elements).  Compensated fp32 and fp64, whose
+// scans are bound by arithmetic (TwoSum pairs; fp64 adds), take the two-pass
+// scan (their entry points decide that before calling scan_flat).
 constexpr uint64_t kAutoPartitionedBytes = 128ull << 20;
 
 int64_t partition_chunk_tiles(const Variant& v, size_t esz) {
@@ -276,9 +277,9 @@ gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n,
     p.exclusive = exclusive;
     cudaGetLastError();  // clear a stale, non-sticky error of an earlier call
     if (algo == GBSCAN_ALGO_AUTO)
-        algo = (v.partitioned && static_cast<uint64_t>(n) * esz >= kAutoPartitionedBytes)
+        algo = (esz == 4 && v.partitioned && static_cast<uint64_t>(n) * esz >= kAutoPartitionedBytes)
                    ? GBSCAN_ALGO_PARTITIONED
-                   : GBSCAN_ALGO_TWO_PASS;
+                   : GBSCAN_ALGO_SINGLE_PASS;
     if (algo == GBSCAN_ALGO_PARTITIONED) {
         if (!v.partitioned) return GBSCAN_ERR_UNSUPPORTED;
         p.chunk_tiles = partition_chunk_tiles(v, esz);
@@ -486,8 +487,18 @@ GBSCAN_FLAT(scan_inclusive_i64, int64_t, family_scan_i64, 0)
 GBSCAN_FLAT(scan_exclusive_i64, int64_t, family_scan_i64, 1)
 GBSCAN_FLAT(scan_inclusive_u32, uint32_t, family_scan_i32, 0)
 GBSCAN_FLAT(scan_exclusive_u32, uint32_t, family_scan_i32, 1)
-GBSCAN_FLAT(scan_inclusive_f64, double, family_scan_f64, 0)
-GBSCAN_FLAT(scan_exclusive_f64, double, family_scan_f64, 1)
+// fp64 is bound by its adds on this part: AUTO takes the two-pass scan
+#define GBSCAN_FLAT_F64(NAME, EXCL)                                                            \
+    gbscan_status NAME(const double* in, double* out, int64_t n, void* ws, size_t ws_bytes,   \
+                       gbscan_algo algo, int variant, cudaStream_t stream) {                  \
+        GBSCAN_NVTX_RANGE(#NAME);                                                             \
+        if (algo == GBSCAN_ALGO_AUTO) algo = GBSCAN_ALGO_TWO_PASS;                             \
+        return scan_flat(family_scan_f64(), in, out, n, sizeof(double), EXCL, ws, ws_bytes,   \
+                         algo, variant, stream);                                              \
+    }
+
+GBSCAN_FLAT_F64(scan_inclusive_f64, 0)
+GBSCAN_FLAT_F64(scan_exclusive_f64, 1)
 
 static gbscan_status scan_f32_impl(const float* in, float* out, int64_t n, gbscan_f32_mode mode,
                                    int excl, void* ws, size_t ws_bytes, gbscan_algo algo,

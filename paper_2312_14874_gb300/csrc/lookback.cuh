@@ -4,8 +4,9 @@
 //
 //   loader warp   claims a tile (one atomic per tile, only once a stage is
 //                 free) and starts a 1-D TMA bulk copy of it into that stage
-//                 (a ragged or misaligned tile is copied element-wise, padded
-//                 with the operator's neutral element);                    [a1]
+//                 (a ragged or misaligned tile: its aligned body by one bulk
+//                 copy, the rest by the lanes, padded with the operator's
+//                 neutral element);                                         [a1]
 //   stage agents  one warp per stage: as soon as the stage's data lands it
 //                 sums the tile from shared memory, publishes the aggregate,
 //                 runs the two-level decoupled look-back (tiles of its 16-tile
@@ -187,6 +188,10 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_scan_kernel(c
     Header* hdr = p.hdr;
     const int64_t num_tiles = p.num_tiles;
 
+    // the loader's first claim goes out before the block's set-up, so that
+    // its round trip overlaps it
+    unsigned int first_claim = 0;
+    if (warp == LOAD_WARP && lane == 0) first_claim = atomicAdd(&hdr->tile_counter, 1u);
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&c.full[s], 1);
@@ -222,7 +227,8 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_scan_kernel(c
             if (use > 0 && !warp_wait(&c.empty[s], (use - 1) & 1u, role_limit, hdr, epoch, lane))
                 break;
             long long claimed = 0;
-            if (lane == 0) claimed = static_cast<long long>(atomicAdd(&hdr->tile_counter, 1u));
+            if (lane == 0)
+                claimed = static_cast<long long>(k == 0 ? first_claim : atomicAdd(&hdr->tile_counter, 1u));
             const int64_t tile = __shfl_sync(0xffffffffu, claimed, 0);
             if (tile >= num_tiles) {
                 // no tiles left (or an aborted launch): an end sentinel in this
