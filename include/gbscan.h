@@ -6,13 +6,18 @@
  * is y_k = a_0 + ... + a_k; the exclusive scan is y_0 = 0, y_k = a_0 + ... +
  * a_{k-1}.  The paper's algorithms are multithreaded two-pass CPU schemes
  * (Section 2.1, Figure 1) and in-register SIMD scans (Section 3, Listing 1);
- * this library computes the same result on the GPU with a single-pass chained
- * scan with decoupled look-back, and keeps a two-pass reduce-then-scan (the
- * paper's "Accumulate + Prefix Sum", Figure 1b) as a comparison.
+ * this library computes the same result on the GPU with three algorithms a
+ * caller can pick (gbscan_algo): a single-pass chained scan with decoupled
+ * look-back; the two-pass reduce-then-scan (the paper's "Accumulate + Prefix
+ * Sum", Figure 1b); and the partitioned scan (Section 2.2, Figure 2) with the
+ * GPU's L2 as the cache, whose second pass over each chunk reads it from L2.
+ * GBSCAN_ALGO_AUTO takes the partitioned scan for large 4-byte arrays and the
+ * single-pass scan for smaller ones and for int64 (see the plain scans).
  *
  * Conventions for every entry point:
  *  - Pointers named in/out/offsets/grad_* and the workspace are DEVICE
- *    pointers owned by the caller.  The library allocates nothing.
+ *    pointers owned by the caller (scan_inclusive_i32_host takes host
+ *    arrays).  The library allocates no device memory.
  *  - All work is enqueued on `stream` and is asynchronous; nothing blocks
  *    except scan_get_device_status().
  *  - `out == in` (in place, the paper's default, Section 2) is allowed; any
@@ -26,7 +31,7 @@
  *    bounded wait that ran out, malformed segment offsets) are recorded in the
  *    workspace and returned by scan_get_device_status().
  *  - Full speed needs `in` and `out` 16-byte aligned; other alignments are
- *    handled by a slower element-wise path.
+ *    handled by a slower path (lanes instead of bulk copies).
  *  - The library never aborts, traps or prints.
  *
  * Workspace: query its size with gbscan_workspace_size(), allocate it on the

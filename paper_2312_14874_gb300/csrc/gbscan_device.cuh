@@ -1,40 +1,30 @@
-// gbscan_device.cuh — device code of the prefix-sum library (sm_103a).
+// gbscan_device.cuh — shared device definitions of the prefix-sum library
+// (sm_103a): the workspace layout (header, tile records, epoch-tagged status
+// words and pairs), the PTX helpers (mbarriers, 1-D TMA bulk copies, L2
+// policies, polling loads, relaxed stores), the operators (+ over int32,
+// int64, fp32, fp64 and compensated fp32 pairs; running maximum and minimum),
+// status publication and reading, and the two-level decoupled look-back:
 //
-// One templated tile kernel implements every scan in the library:
+//   look-back : a tile publishes its aggregate, then one warp reads the status
+//               of its predecessors and folds their values until it meets a
+//               published inclusive prefix, in two levels (the tiles of its
+//               16-tile group, then group words); the tile then publishes its
+//               own inclusive prefix.  This is the adjacent-only
+//               synchronisation that Section 2.2.1 offers in place of a
+//               counting barrier (citing StreamScan), with the decoupled
+//               aggregate / prefix states of Merrill and Garland's single-pass
+//               scan, and it plays the role of the paper's sums array
+//               (Section 2.1, Figure 1).
 //
-//   tile load    : 1-D TMA bulk copy (cp.async.bulk) of a whole tile into shared
-//                  memory, completing on an mbarrier; an element-wise path covers
-//                  the ragged last tile and misaligned arrays.
-//   thread scan  : each thread owns ITEMS consecutive elements (the "vertical"
-//                  per-lane chunk of Section 3.2) read with conflict-free 128-bit
-//                  shared loads, and reduces them sequentially in registers.
-//   warp scan    : Hillis-Steele log-step scan over the 32 thread totals with
-//                  __shfl_up_sync (the in-register scan of Section 3.1, Listing 1,
-//                  with warp lanes in place of AVX-512 lanes).
-//   block scan   : warp totals through shared memory, scanned by warp 0; the last
-//                  value is the tile total, broadcast like the carry vector of
-//                  Section 3.1.
-//   look-back    : the tile publishes its total, then the stage's look-back
-//                  agent warp reads the status of 32 x LB predecessors per round
-//                  and folds their totals until it meets a published inclusive
-//                  prefix (two levels: 16-tile groups publish group states too);
-//                  the tile then publishes its own inclusive prefix.  This is
-//                  the "synchronise only with adjacent threads" alternative to
-//                  the counting barrier that Section 2.2.1 mentions
-//                  (StreamScan), with the decoupled aggregate/prefix states of
-//                  Merrill and Garland's single-pass scan, and it plays the role
-//                  of the paper's sums array (Section 2.1, Figure 1).
-//   store        : results are written back over the tile in shared memory and
-//                  leave with one TMA bulk store.
-//
-// The same tile code, with a mode parameter, gives the two-pass comparison of
-// the paper's "Accumulate + Prefix Sum" (Figure 1b): a reduce-only pass and a
-// scan-with-offset pass around a one-block scan of the tile sums; and
-// partitioned.cuh builds the cache-friendly partitioned scan (Section 2.2) from
-// the same pieces.
+// The kernels are in lookback.cuh (single-pass chained scan), kernels.cuh
+// (two-pass comparison, and the warp-specialised chained kernel used by the
+// segmented and long-row scans), partitioned.cuh (the cache-partitioned scan,
+// Section 2.2), rows.cuh (row scans and their backward) and compact.cuh
+// (stream compaction).
 //
 // Every wait is bounded (a %globaltimer deadline); a wait that runs out records
-// GBSCAN_ERR_TIMEOUT in the workspace and the kernel still finishes.
+// GBSCAN_ERR_TIMEOUT in the workspace, aborts the launch, and the kernel still
+// finishes.
 #pragma once
 
 #include <cstdint>

@@ -1,6 +1,9 @@
 // kernels.cuh — the tile kernels.
 //
-// ws_scan_kernel: the single-pass chained scan, warp-specialised.
+// ws_scan_kernel: a chained scan with decoupled look-back, warp-specialised,
+//   for the segmented (offset heads) and long-row (row heads, forward and
+//   reverse) scans; the plain scans use lookback.cuh, which holds waiting
+//   tiles in registers instead of shared memory.
 //   loader warp     claims tiles in order (dynamic tile ids) and starts a TMA
 //                   bulk copy of each into a free pipeline stage;
 //   stage agents    one warp per pipeline stage: as soon as the stage's data
