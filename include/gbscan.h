@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define GBSCAN_ABI_VERSION 1
+#define GBSCAN_ABI_VERSION 2
 
 typedef enum {
     GBSCAN_OK = 0,
@@ -65,11 +65,14 @@ typedef enum {
 } gbscan_status;
 
 typedef enum {
-    GBSCAN_ALGO_AUTO = 0,        /* PARTITIONED from 128 MiB of input, else TWO_PASS */
-    GBSCAN_ALGO_SINGLE_PASS = 1, /* chained scan with decoupled look-back */
-    GBSCAN_ALGO_TWO_PASS = 2,    /* reduce tiles, scan the tile sums, scan with offsets */
-    GBSCAN_ALGO_PARTITIONED = 3  /* cache-friendly partitioned two-pass (Section 2.2):
-                                    per L2-sized chunk, reduce then scan from L2, one launch */
+    GBSCAN_ALGO_AUTO = 0,         /* by size and type; see the plain scans below */
+    GBSCAN_ALGO_SINGLE_PASS = 1,  /* chained scan with decoupled look-back */
+    GBSCAN_ALGO_TWO_PASS = 2,     /* reduce tiles, scan the tile sums, scan with offsets */
+    GBSCAN_ALGO_PARTITIONED = 3,  /* cache-friendly partitioned two-pass (Section 2.2):
+                                     per L2-sized chunk, reduce then scan from L2, one launch */
+    GBSCAN_ALGO_RESIDENT = 4      /* small inputs, one launch: every tile held in shared
+                                     memory across a grid barrier between the reduce and
+                                     the scan (Figure 1b with Section 2.2's partitioning) */
 } gbscan_algo;
 
 typedef enum {
@@ -118,11 +121,18 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
  *               environment variable GBSCAN_CHUNK_BYTES; each chunk is reduced tile by
  *               tile, its tile sums are scanned, and it is scanned a second time while
  *               still in L2, overlapped with the reduction of the chunk four ahead,
- *               GBSCAN_CHUNK_LAG), or AUTO (4-byte elements: PARTITIONED for inputs of
- *               128 MiB or more, SINGLE_PASS below; int64: SINGLE_PASS; compensated
- *               fp32 and fp64: TWO_PASS; the fastest choices measured on GB300).
+ *               GBSCAN_CHUNK_LAG), RESIDENT (one cooperative launch, one block per tile
+ *               of 5120 4-byte or 2560 8-byte elements, every block resident at once:
+ *               each block keeps its tile in shared memory, writes the tile's sum, and
+ *               after a grid-wide barrier adds the sums of the tiles before it; for
+ *               inputs of at most SMs x blocks-per-SM tiles, gbscan_resident_max_n;
+ *               larger inputs return GBSCAN_ERR_UNSUPPORTED), or AUTO (RESIDENT where it fits;
+ *               above that, 4-byte elements: PARTITIONED for inputs of 128 MiB or more,
+ *               SINGLE_PASS below; int64: SINGLE_PASS; compensated fp32 and fp64:
+ *               TWO_PASS; the fastest choices measured on GB300).
  *   variant   : launch shape (threads, items per thread, pipeline stages), 0 = default;
- *               see gbscan_num_variants / gbscan_variant_info.
+ *               see gbscan_num_variants / gbscan_variant_info.  RESIDENT has one shape:
+ *               the variant is checked but does not change the launch.
  *   mode      : (f32 only) plain fp32 or compensated two-sum carries.
  */
 gbscan_status scan_inclusive_i32(const int32_t* in, int32_t* out, int64_t n, void* ws,
@@ -317,6 +327,18 @@ gbscan_status gbscan_set_debug(void* ws, size_t ws_bytes, uint32_t spin_limit_us
 int gbscan_num_variants(gbscan_dtype dtype, gbscan_kind kind);
 gbscan_status gbscan_variant_info(gbscan_dtype dtype, gbscan_kind kind, int variant,
                                   int* threads, int* items, int* stages, int* tile);
+
+/* The largest n that GBSCAN_ALGO_RESIDENT takes for a plain scan of `dtype` on
+ * the current device: the blocks that fit the device at once (SMs x blocks per
+ * SM, from the CUDA occupancy calculator) times the tile (5120 4-byte or 2560
+ * 8-byte elements).  kind: GBSCAN_KIND_SCAN (for GBSCAN_F32, `mode` picks
+ * plain or compensated sums; other types ignore it), GBSCAN_KIND_SCAN_MAX or
+ * GBSCAN_KIND_SCAN_MIN.  Writes *n.  Returns GBSCAN_ERR_INVALID_ARG for a null
+ * `n`, an unknown dtype or mode, GBSCAN_ERR_UNSUPPORTED for other kinds or
+ * combinations without a resident scan, GBSCAN_ERR_CUDA if CUDA cannot report
+ * the device or the occupancy. */
+gbscan_status gbscan_resident_max_n(gbscan_dtype dtype, gbscan_kind kind, gbscan_f32_mode mode,
+                                    int64_t* n);
 
 /* Device-to-device copy of `bytes` bytes with a vectorised copy kernel: the
  * bandwidth reference the scan is measured against. */

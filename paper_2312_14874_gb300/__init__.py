@@ -31,7 +31,7 @@ from ._capi import GbscanError
 __all__ = [
     "inclusive", "exclusive", "scan", "segmented", "rows", "backward", "cumsum",
     "device_status", "copy_", "Workspace", "workspace_bytes", "set_debug", "GbscanError",
-    "num_variants", "variant_info", "compact", "inclusive_host",
+    "num_variants", "variant_info", "resident_max_n", "compact", "inclusive_host",
 ]
 
 _DTYPES = {
@@ -42,7 +42,8 @@ _DTYPES = {
     torch.uint32: (_capi.U32, "u32"),
 }
 _ALGOS = {"auto": _capi.ALGO_AUTO, "single_pass": _capi.ALGO_SINGLE_PASS,
-          "two_pass": _capi.ALGO_TWO_PASS, "partitioned": _capi.ALGO_PARTITIONED}
+          "two_pass": _capi.ALGO_TWO_PASS, "partitioned": _capi.ALGO_PARTITIONED,
+          "resident": _capi.ALGO_RESIDENT}
 
 
 def _stream_handle(device) -> int:
@@ -377,3 +378,14 @@ def variant_info(dtype: torch.dtype, kind: int, variant: int) -> dict:
                                                 ctypes.byref(s), ctypes.byref(tile)),
                 "gbscan_variant_info")
     return {"threads": t.value, "items": i.value, "stages": s.value, "tile": tile.value}
+
+
+def resident_max_n(dtype: torch.dtype, kind: int = _capi.KIND_SCAN, compensated: bool = False) -> int:
+    """The largest input that ``algo="resident"`` takes for this dtype and kind
+    (plain scan, running max or min) on the current device."""
+    import ctypes
+    n = ctypes.c_int64(0)
+    mode = _capi.F32_COMPENSATED if compensated else _capi.F32_PLAIN
+    _capi.check(_capi.lib().gbscan_resident_max_n(_DTYPES[dtype][0], kind, mode, ctypes.byref(n)),
+                "gbscan_resident_max_n")
+    return n.value

@@ -24,7 +24,7 @@ STATUS_NAMES = {
     ERR_UNSUPPORTED: "GBSCAN_ERR_UNSUPPORTED",
 }
 # gbscan_algo
-ALGO_AUTO, ALGO_SINGLE_PASS, ALGO_TWO_PASS, ALGO_PARTITIONED = 0, 1, 2, 3
+ALGO_AUTO, ALGO_SINGLE_PASS, ALGO_TWO_PASS, ALGO_PARTITIONED, ALGO_RESIDENT = 0, 1, 2, 3, 4
 # gbscan_f32_mode
 F32_PLAIN, F32_COMPENSATED = 0, 1
 # gbscan_dtype
@@ -60,6 +60,7 @@ _SIGNATURES = {
     "gbscan_set_debug": [_vp, _sz, _u32, _i64, _u32, _vp],
     "gbscan_num_variants": [_i32, _i32],
     "gbscan_variant_info": [_i32, _i32, _i32] + [ctypes.POINTER(ctypes.c_int)] * 4,
+    "gbscan_resident_max_n": [_i32, _i32, _i32, ctypes.POINTER(ctypes.c_int64)],
     "gbscan_copy": [_vp, _vp, _sz, _vp],
     "gbscan_status_string": [_i32],
     "gbscan_abi_version": [],
@@ -79,7 +80,7 @@ _SIGNATURES = {
 _RESTYPE = {"gbscan_status_string": ctypes.c_char_p, "gbscan_num_variants": ctypes.c_int,
             "gbscan_abi_version": ctypes.c_int}
 
-ABI_VERSION = 1
+ABI_VERSION = 2
 
 
 def exported_names() -> list[str]:

@@ -49,7 +49,8 @@ def _table(key: str) -> dict:
         return _tables[key]
 
 
-ALGOS = ("single_pass", "two_pass", "partitioned")
+ALGOS = ("single_pass", "two_pass", "partitioned", "resident")
+SINGLE_SHAPE_ALGOS = ("resident",)  # one launch shape: timed as variant 0 only
 
 
 def _entry(kind_key: str, n: int):
@@ -91,7 +92,17 @@ def choose(kind_key: str, dtype_key: str, n: int, algo: str = "auto") -> tuple[s
     return algo, int(entry)
 
 
+_flush_buf: torch.Tensor | None = None
+
+
 def _time_ms(fn, reps: int = 10, warmup: int = 3) -> float:
+    """Device time of fn (CUDA events, trimmed mean).  Before each rep a 256 MiB fill
+    keeps the GPU busy while the host enqueues fn (so the host's enqueue time
+    is not timed, which at small sizes would dwarf the kernel) and evicts the
+    input from L2, as the benchmark does."""
+    global _flush_buf
+    if _flush_buf is None:
+        _flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=torch.cuda.current_device())
     for _ in range(warmup):
         fn()
     stream = torch.cuda.current_stream()
@@ -99,13 +110,18 @@ def _time_ms(fn, reps: int = 10, warmup: int = 3) -> float:
     end = torch.cuda.Event(enable_timing=True)
     times = []
     for _ in range(reps):
+        _flush_buf.fill_(1)
         start.record(stream)
         fn()
         end.record(stream)
         end.synchronize()
         times.append(start.elapsed_time(end))
+    # events tick in steps of about 2 us on GB300: a trimmed mean resolves
+    # finer differences than the median between small kernels
     times.sort()
-    return times[len(times) // 2]
+    k = len(times) // 10
+    kept = times[k:len(times) - k] or times
+    return sum(kept) / len(kept)
 
 
 def tune(sizes_log2=(20, 22, 24, 26, 28, 30), write: bool = True, families=None,
@@ -155,9 +171,12 @@ def tune(sizes_log2=(20, 22, 24, 26, 28, 30), write: bool = True, families=None,
             y = torch.empty_like(x)
             entry, best_t = {}, None
             for algo in ALGOS:
+                if algo == "resident" and (1 << lg) > gb.resident_max_n(dtype, compensated=comp):
+                    continue
+                nva = 1 if algo in SINGLE_SHAPE_ALGOS else nv
                 times = [_time_ms(lambda: gb.scan(x, out=y, algo=algo, variant=v, compensated=comp))
-                         for v in range(nv)]
-                v = min(range(nv), key=lambda i: times[i])
+                         for v in range(nva)]
+                v = min(range(nva), key=lambda i: times[i])
                 entry[algo] = v
                 if best_t is None or times[v] < best_t:
                     best_t, entry["best"] = times[v], f"{algo}:{v}"
@@ -237,7 +256,8 @@ def tune(sizes_log2=(20, 22, 24, 26, 28, 30), write: bool = True, families=None,
                 existing = json.load(f)
         except (OSError, ValueError):
             pass
-        existing.update(result)
+        for fam, entries in result.items():  # merge by size bucket
+            existing.setdefault(fam, {}).update(entries)
         with open(path, "w") as f:
             json.dump(existing, f, indent=1, sort_keys=True)
         with _lock:

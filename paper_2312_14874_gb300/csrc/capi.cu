@@ -257,29 +257,51 @@ int64_t partition_chunk_lag() {
     return lag > 8 ? 8 : lag;
 }
 
+// Whether the family's resident scan takes n elements on the current device.
+bool resident_fits(const Family& fam, int64_t n) {
+    if (!fam.resident) return false;
+    const int64_t cap = fam.resident_capacity();
+    return cap > 0 && (n + fam.resident_tile - 1) / fam.resident_tile <= cap;
+}
+
+// GBSCAN_ALGO_AUTO for the scans bound by arithmetic (compensated fp32, fp64):
+// the resident scan where it fits, the two-pass scan above.
+gbscan_algo auto_arith_bound(const Family& fam, int64_t n, gbscan_algo algo) {
+    if (algo != GBSCAN_ALGO_AUTO) return algo;
+    return resident_fits(fam, n) ? GBSCAN_ALGO_RESIDENT : GBSCAN_ALGO_TWO_PASS;
+}
+
 gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n, size_t esz,
                         int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                         cudaStream_t stream) {
     if (n < 0) return GBSCAN_ERR_INVALID_ARG;
     if (algo != GBSCAN_ALGO_AUTO && algo != GBSCAN_ALGO_SINGLE_PASS &&
-        algo != GBSCAN_ALGO_TWO_PASS && algo != GBSCAN_ALGO_PARTITIONED)
+        algo != GBSCAN_ALGO_TWO_PASS && algo != GBSCAN_ALGO_PARTITIONED &&
+        algo != GBSCAN_ALGO_RESIDENT)
         return GBSCAN_ERR_INVALID_ARG;
     if (variant < 0 || variant >= fam.num_variants) return GBSCAN_ERR_INVALID_ARG;
     if (n == 0) return GBSCAN_OK;
     gbscan_status st = check_io(in, out, n, esz);
     if (st != GBSCAN_OK) return st;
     const Variant& v = fam.variants[variant];
-    const int64_t tiles = (n + v.tile - 1) / v.tile;
-    if (tiles > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
-    st = check_ws(ws, ws_bytes, records_for(n, v.tile));
+    if (algo == GBSCAN_ALGO_AUTO) {
+        if (resident_fits(fam, n))
+            algo = GBSCAN_ALGO_RESIDENT;
+        else if (esz == 4 && v.partitioned &&
+                 static_cast<uint64_t>(n) * esz >= kAutoPartitionedBytes)
+            algo = GBSCAN_ALGO_PARTITIONED;
+        else
+            algo = GBSCAN_ALGO_SINGLE_PASS;
+    }
+    if (algo == GBSCAN_ALGO_RESIDENT && !resident_fits(fam, n)) return GBSCAN_ERR_UNSUPPORTED;
+    const int tile = algo == GBSCAN_ALGO_RESIDENT ? fam.resident_tile : v.tile;
+    if ((n + tile - 1) / tile > kMaxTiles) return GBSCAN_ERR_UNSUPPORTED;
+    st = check_ws(ws, ws_bytes, records_for(n, tile));
     if (st != GBSCAN_OK) return st;
-    Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
+    Params p = make_params(in, out, n, tile, ws, ws_bytes);
     p.exclusive = exclusive;
     cudaGetLastError();  // clear a stale, non-sticky error of an earlier call
-    if (algo == GBSCAN_ALGO_AUTO)
-        algo = (esz == 4 && v.partitioned && static_cast<uint64_t>(n) * esz >= kAutoPartitionedBytes)
-                   ? GBSCAN_ALGO_PARTITIONED
-                   : GBSCAN_ALGO_SINGLE_PASS;
+    if (algo == GBSCAN_ALGO_RESIDENT) return from_cuda(fam.resident(p, stream));
     if (algo == GBSCAN_ALGO_PARTITIONED) {
         if (!v.partitioned) return GBSCAN_ERR_UNSUPPORTED;
         p.chunk_tiles = partition_chunk_tiles(v, esz);
@@ -492,9 +514,9 @@ GBSCAN_FLAT(scan_exclusive_u32, uint32_t, family_scan_i32, 1)
     gbscan_status NAME(const double* in, double* out, int64_t n, void* ws, size_t ws_bytes,   \
                        gbscan_algo algo, int variant, cudaStream_t stream) {                  \
         GBSCAN_NVTX_RANGE(#NAME);                                                             \
-        if (algo == GBSCAN_ALGO_AUTO) algo = GBSCAN_ALGO_TWO_PASS;                             \
-        return scan_flat(family_scan_f64(), in, out, n, sizeof(double), EXCL, ws, ws_bytes,   \
-                         algo, variant, stream);                                              \
+        const Family& fam = family_scan_f64();                                                \
+        return scan_flat(fam, in, out, n, sizeof(double), EXCL, ws, ws_bytes,                 \
+                         auto_arith_bound(fam, n, algo), variant, stream);                    \
     }
 
 GBSCAN_FLAT_F64(scan_inclusive_f64, 0)
@@ -505,7 +527,7 @@ static gbscan_status scan_f32_impl(const float* in, float* out, int64_t n, gbsca
                                    int variant, cudaStream_t stream) {
     if (mode != GBSCAN_F32_PLAIN && mode != GBSCAN_F32_COMPENSATED) return GBSCAN_ERR_INVALID_ARG;
     const Family& fam = mode == GBSCAN_F32_COMPENSATED ? family_scan_f32c() : family_scan_f32();
-    if (mode == GBSCAN_F32_COMPENSATED && algo == GBSCAN_ALGO_AUTO) algo = GBSCAN_ALGO_TWO_PASS;
+    if (mode == GBSCAN_F32_COMPENSATED) algo = auto_arith_bound(fam, n, algo);
     return scan_flat(fam, in, out, n, sizeof(float), excl, ws, ws_bytes, algo, variant, stream);
 }
 
@@ -833,6 +855,22 @@ const char* gbscan_status_string(gbscan_status status) {
     case GBSCAN_ERR_UNSUPPORTED: return "unsupported size or option";
     }
     return "unknown status";
+}
+
+gbscan_status gbscan_resident_max_n(gbscan_dtype dtype, gbscan_kind kind, gbscan_f32_mode mode,
+                                    int64_t* n) {
+    if (n == nullptr || !valid_dtype(dtype)) return GBSCAN_ERR_INVALID_ARG;
+    if (mode != GBSCAN_F32_PLAIN && mode != GBSCAN_F32_COMPENSATED) return GBSCAN_ERR_INVALID_ARG;
+    if (kind != GBSCAN_KIND_SCAN && kind != GBSCAN_KIND_SCAN_MAX && kind != GBSCAN_KIND_SCAN_MIN)
+        return GBSCAN_ERR_UNSUPPORTED;
+    const Family* f = (kind == GBSCAN_KIND_SCAN && dtype == GBSCAN_F32 && mode == GBSCAN_F32_COMPENSATED)
+                          ? &family_scan_f32c()
+                          : family_for(dtype, kind);
+    if (f == nullptr || !f->resident) return GBSCAN_ERR_UNSUPPORTED;
+    const int64_t cap = f->resident_capacity();
+    if (cap <= 0) return GBSCAN_ERR_CUDA;
+    *n = cap * f->resident_tile;
+    return GBSCAN_OK;
 }
 
 int gbscan_abi_version(void) { return GBSCAN_ABI_VERSION; }

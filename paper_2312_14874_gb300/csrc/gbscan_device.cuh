@@ -634,6 +634,10 @@ __device__ __forceinline__ typename Op::Acc shfl_down_acc(typename Op::Acc v, in
     return Op::from_bits(__shfl_down_sync(0xffffffffu, Op::to_bits(v), d));
 }
 template <class Op>
+__device__ __forceinline__ typename Op::Acc shfl_xor_acc(typename Op::Acc v, int m) {
+    return Op::from_bits(__shfl_xor_sync(0xffffffffu, Op::to_bits(v), m));
+}
+template <class Op>
 __device__ __forceinline__ typename Op::Acc shfl_idx_acc(typename Op::Acc v, int src) {
     return Op::from_bits(__shfl_sync(0xffffffffu, Op::to_bits(v), src));
 }

@@ -6,6 +6,7 @@
 
 #include "kernels.cuh"
 #include "lookback.cuh"
+#include "resident.cuh"
 #include "partitioned.cuh"
 #include "rows.cuh"
 #include "compact.cuh"
@@ -14,6 +15,7 @@ namespace gbscan {
 
 using LaunchFn = cudaError_t (*)(const Params&, cudaStream_t);
 using SumsFn = cudaError_t (*)(unsigned long long*, int64_t, cudaStream_t);
+using CapacityFn = int64_t (*)();
 
 // One launch shape of a kernel family.
 struct Variant {
@@ -32,6 +34,9 @@ struct Family {
     int num_variants;
     const Variant* variants;
     SumsFn scan_sums;  // two-pass: exclusive scan of the tile sums (null where not built)
+    LaunchFn resident;            // the resident scan (one block per tile of resident_tile
+    int resident_tile;            //   elements), or null where not built;
+    CapacityFn resident_capacity; //   the most tiles it takes on the current device
 };
 
 int device_sm_count(int device);
@@ -91,6 +96,61 @@ cudaError_t launch_lb(const Params& p, cudaStream_t stream) {
     return launch_persistent(lb_scan_kernel<Op, NW, NV, STAGES, LB, MINB>, lb_threads<NW, STAGES>(),
                              lb_smem_bytes<Op, NW, NV, STAGES>(), occ_cache, p, stream);
 }
+
+// Blocks of the resident scan that fit the current device at once (SMs x
+// blocks per SM, at most kResidentMaxTiles), or -1 if CUDA cannot say.
+template <class Op, int THREADS, int ITEMS, int MINB>
+int64_t resident_capacity() {
+    static std::atomic<int> occ_cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    int occ = (dev >= 0 && dev < 64) ? occ_cache[dev].load(std::memory_order_relaxed) : 0;
+    if (occ <= 0) {
+        auto kern = resident_scan_kernel<Op, THREADS, ITEMS, MINB>;
+        const int smem = resident_smem_bytes<Op, THREADS, ITEMS>();
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, smem) != cudaSuccess)
+            return -1;
+        if (occ <= 0) return -1;
+        if (dev >= 0 && dev < 64) occ_cache[dev].store(occ, std::memory_order_relaxed);
+    }
+    const int sms = device_sm_count(dev);
+    if (sms <= 0) return -1;
+    const int64_t cap = static_cast<int64_t>(sms) * occ;
+    return cap < kResidentMaxTiles ? cap : kResidentMaxTiles;
+}
+
+// One block per tile, all resident: a cooperative launch, which the runtime
+// starts only when every block can run at once.  The host checks the tile
+// count against resident_capacity first.
+template <class Op, int THREADS, int ITEMS, int MINB>
+cudaError_t launch_resident(const Params& p, cudaStream_t stream) {
+    const int64_t cap = resident_capacity<Op, THREADS, ITEMS, MINB>();
+    if (cap < 0) return cudaErrorInvalidConfiguration;
+    if (p.num_tiles < 1 || p.num_tiles > cap) return cudaErrorCooperativeLaunchTooLarge;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(p.num_tiles));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = static_cast<size_t>(resident_smem_bytes<Op, THREADS, ITEMS>());
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, resident_scan_kernel<Op, THREADS, ITEMS, MINB>, p);
+}
+
+// The resident scan of a plain family: 256 threads x 80 bytes of items (20
+// KB tiles: 5120 4-byte or 2560 8-byte elements); 4 blocks per SM (608 tiles
+// on 152 SMs) for 4-byte accumulators, 3 for 8-byte and pair accumulators.
+#define GBSCAN_RESIDENT_ITEMS(OP) (80 / static_cast<int>(sizeof(OP::T)))
+#define GBSCAN_RESIDENT_MINB(OP) (sizeof(OP::Acc) == 4 ? 4 : 3)
+#define GBSCAN_RESIDENT(OP)                                                                    \
+    &launch_resident<OP, 256, GBSCAN_RESIDENT_ITEMS(OP), GBSCAN_RESIDENT_MINB(OP)>,              \
+        256 * GBSCAN_RESIDENT_ITEMS(OP),                                                       \
+        &resident_capacity<OP, 256, GBSCAN_RESIDENT_ITEMS(OP), GBSCAN_RESIDENT_MINB(OP)>
 
 template <class Op, int THREADS, int ITEMS, int STAGES, int MODE>
 cudaError_t launch_tp(const Params& p, cudaStream_t stream) {

@@ -14,7 +14,7 @@ static const Variant kScanF32[] = {
 };
 
 const Family& family_scan_f32() {
-    static const Family f{6, kScanF32, &launch_scan_sums<OpF32>};
+    static const Family f{6, kScanF32, &launch_scan_sums<OpF32>, GBSCAN_RESIDENT(OpF32)};
     return f;
 }
 

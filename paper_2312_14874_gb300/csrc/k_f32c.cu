@@ -14,7 +14,7 @@ static const Variant kScanF32C[] = {
 };
 
 const Family& family_scan_f32c() {
-    static const Family f{6, kScanF32C, &launch_scan_sums<OpF32C>};
+    static const Family f{6, kScanF32C, &launch_scan_sums<OpF32C>, GBSCAN_RESIDENT(OpF32C)};
     return f;
 }
 

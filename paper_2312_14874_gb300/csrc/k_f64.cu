@@ -13,7 +13,7 @@ static const Variant kScanF64[] = {
 };
 
 const Family& family_scan_f64() {
-    static const Family f{6, kScanF64, &launch_scan_sums<OpF64>};
+    static const Family f{6, kScanF64, &launch_scan_sums<OpF64>, GBSCAN_RESIDENT(OpF64)};
     return f;
 }
 

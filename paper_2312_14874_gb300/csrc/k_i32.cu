@@ -14,7 +14,7 @@ static const Variant kScanI32[] = {
 };
 
 const Family& family_scan_i32() {
-    static const Family f{6, kScanI32, &launch_scan_sums<OpI32>};
+    static const Family f{6, kScanI32, &launch_scan_sums<OpI32>, GBSCAN_RESIDENT(OpI32)};
     return f;
 }
 

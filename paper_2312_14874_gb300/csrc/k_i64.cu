@@ -13,7 +13,7 @@ static const Variant kScanI64[] = {
 };
 
 const Family& family_scan_i64() {
-    static const Family f{6, kScanI64, &launch_scan_sums<OpI64>};
+    static const Family f{6, kScanI64, &launch_scan_sums<OpI64>, GBSCAN_RESIDENT(OpI64)};
     return f;
 }
 

@@ -13,7 +13,7 @@ namespace gbscan {
         GBSCAN_VARIANT_ALL(OP, 8, 28, 4, 2, 2, 3, 2),                                           \
     };                                                                                          \
     const Family& FN() {                                                                        \
-        static const Family f{3, kVariants##OP, &launch_scan_sums<OP>};                         \
+        static const Family f{3, kVariants##OP, &launch_scan_sums<OP>, GBSCAN_RESIDENT(OP)};                         \
         return f;                                                                               \
     }
 

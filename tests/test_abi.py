@@ -124,6 +124,18 @@ def test_variant_table():
     assert L.gbscan_num_variants(_capi.I64, _capi.KIND_SEGMENTED) == 0
 
 
+def test_resident_max_n_arguments():
+    L = _capi.lib()
+    n = ctypes.c_int64(0)
+    assert L.gbscan_resident_max_n(_capi.I32, _capi.KIND_SCAN, 0, None) == _capi.ERR_INVALID_ARG
+    assert L.gbscan_resident_max_n(99, _capi.KIND_SCAN, 0, ctypes.byref(n)) == _capi.ERR_INVALID_ARG
+    assert L.gbscan_resident_max_n(_capi.F32, _capi.KIND_SCAN, 7, ctypes.byref(n)) == _capi.ERR_INVALID_ARG
+    for kind in (_capi.KIND_ROWS, _capi.KIND_SEGMENTED, _capi.KIND_COMPACT):
+        assert L.gbscan_resident_max_n(_capi.F32, kind, 0, ctypes.byref(n)) == _capi.ERR_UNSUPPORTED
+    assert L.gbscan_resident_max_n(_capi.F64, _capi.KIND_SCAN_MAX, 0, ctypes.byref(n)) == \
+        _capi.ERR_UNSUPPORTED
+
+
 def test_status_strings():
     L = _capi.lib()
     for code in range(7):

@@ -17,7 +17,7 @@ from paper_2312_14874_gb300 import _capi
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 2, 5119, 5120, 5121, 3 * 5120 * 7 + 13, 1_000_003]
-ALGOS = ["single_pass", "two_pass", "partitioned"]
+ALGOS = ["single_pass", "two_pass", "partitioned", "resident"]
 
 
 def dev():
@@ -123,8 +123,7 @@ def test_uint32_sums(algo):
     bit-exact, every variant, inclusive and exclusive."""
     L = _capi.lib()
     s = torch.cuda.current_stream().cuda_stream
-    a_ = {"single_pass": _capi.ALGO_SINGLE_PASS, "two_pass": _capi.ALGO_TWO_PASS,
-          "partitioned": _capi.ALGO_PARTITIONED}[algo]
+    a_ = gb._ALGOS[algo]
     for n in SIZES:
         a = u32_data(n, seed=n % 1000)
         x = to_dev_u32(a)

@@ -128,7 +128,7 @@ def test_race_stress_partitioned_small_chunks(tmp_path, lag):
 LAUNCH_BOUND_S = 1.0
 
 
-@pytest.mark.parametrize("algo", ["single_pass", "partitioned", "two_pass"])
+@pytest.mark.parametrize("algo", ["single_pass", "partitioned", "two_pass", "resident"])
 @pytest.mark.parametrize("dtype", [torch.int32, torch.int64, torch.float32])
 def test_dropped_tile_times_out_and_recovers(dtype, algo):
     """A tile that never publishes (the drop hook) makes the waits on it run out:
@@ -195,7 +195,7 @@ def test_cuda_graph_segmented_replay():
     assert g.device_status() == 0
 
 
-@pytest.mark.parametrize("algo", ["auto", "single_pass", "partitioned"])
+@pytest.mark.parametrize("algo", ["auto", "single_pass", "partitioned", "resident"])
 def test_cuda_graph_plain_scan_replay(algo):
     n = (1 << 20) + 5
     x = torch.empty(n, dtype=torch.float32, device=dev())

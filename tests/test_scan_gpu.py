@@ -79,6 +79,46 @@ def test_scan_sizes_all_variants(dtype_key, algo):
     assert gb.device_status() == 0
 
 
+# The resident scan: one block per tile (5120 4-byte or 2560 8-byte elements),
+# every block resident at once, so at most SMs x blocks-per-SM tiles.
+def resident_limit(dtype_key, compensated=False):
+    torch_dt = {"i32": torch.int32, "i64": torch.int64, "f32": torch.float32,
+                "f64": torch.float64}[dtype_key]
+    lim = gb.resident_max_n(torch_dt, compensated=compensated)
+    sms = torch.cuda.get_device_properties(dev()).multi_processor_count
+    tile = 2560 if dtype_key in ("i64", "f64") else 5120
+    assert lim % (sms * tile) == 0 and 1 <= lim // (sms * tile) <= 8
+    return lim
+
+
+@pytest.mark.parametrize("dtype_key", ["i32", "i64", "f32", "f64"])
+def test_scan_resident(dtype_key):
+    """The size ladder, the largest input the resident scan takes, and one
+    element more (refused with UNSUPPORTED, nothing launched); inclusive and
+    exclusive, in place, plain and compensated, and a misaligned view (the
+    lanes' copies and stores on every tile)."""
+    for comp in ((False, True) if dtype_key == "f32" else (False,)):
+        lim = resident_limit(dtype_key, comp)
+        for n in SIZES + [lim - 1, lim]:
+            a = gen(dtype_key, n, seed=n)
+            x = to_dev(a)
+            for excl in (False, True):
+                y = gb.scan(x, excl, algo="resident", variant=0, compensated=comp).cpu().numpy()
+                check(dtype_key, a, y, excl, compensated=comp)
+            x2 = x.clone()
+            gb.scan(x2, out=x2, algo="resident", variant=0, compensated=comp)
+            check(dtype_key, a, x2.cpu().numpy(), False, compensated=comp)
+        x = torch.zeros(lim + 1, dtype=x.dtype, device=dev())
+        with pytest.raises(_capi.GbscanError) as e:
+            gb.scan(x, algo="resident", variant=0, compensated=comp)
+        assert e.value.status == _capi.ERR_UNSUPPORTED
+    a = gen(dtype_key, 3 * 5120 + 9, seed=5)
+    xb = to_dev(a)[1:]
+    y = gb.scan(xb, algo="resident", variant=0).cpu().numpy()
+    check(dtype_key, a[1:], y, False)
+    assert gb.device_status() == 0
+
+
 @pytest.mark.parametrize("algo", ["single_pass", "two_pass", "partitioned"])
 def test_scan_f32_compensated(algo):
     for v in variants(torch.float32):
