@@ -72,22 +72,6 @@ constexpr int lb_threads() {
     return (NW + 1 + STAGES) * 32;
 }
 
-// Named barrier `id` over NTHREADS threads that also ORs a predicate over them:
-// every thread gets true if any thread passed true.
-template <int NTHREADS>
-__device__ __forceinline__ bool named_barrier_or(int id, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, %2, %3, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"(pred ? 1u : 0u), "r"(id), "n"(NTHREADS)
-        : "memory");
-    return r != 0;
-}
-
 // 16-byte streaming store (the output is not read again by this launch).
 __device__ __forceinline__ void st_stream_v4(void* p, const uint4& v) {
     asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y),

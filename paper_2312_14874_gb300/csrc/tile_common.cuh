@@ -243,6 +243,22 @@ __device__ __forceinline__ uint32_t warp_stage_partial(T* dst, const T* src, int
     return bulk;
 }
 
+// Named barrier `id` over NTHREADS threads that also ORs a predicate over them:
+// every thread gets true if any thread passed true.
+template <int NTHREADS>
+__device__ __forceinline__ bool named_barrier_or(int id, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred ? 1u : 0u), "r"(id), "n"(NTHREADS)
+        : "memory");
+    return r != 0;
+}
+
 template <int NTHREADS>
 __device__ __forceinline__ void named_barrier_sync(int id) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NTHREADS) : "memory");
