@@ -28,6 +28,8 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "gbscan.h"
@@ -610,11 +612,21 @@ struct OpF32C {
         two_sum(s, lo, h2, l2);  // renormalise so |lo| stays below half an ulp of hi
         return make_float2(h2, l2);
     }
-    // a thread-local run: plain fp32 on hi
-    __device__ static void accumulate(Acc& r, T x) { r.x = __fadd_rn(r.x, x); }
-    __device__ static T output(Acc c, Acc l) {
-        return __fadd_rn(c.x, __fadd_rn(__fadd_rn(l.x, c.y), l.y));
+    // short chains inside a tile: the exact error of the hi sum joins lo, and
+    // the pair is not renormalised (after the at most few tens of combines of
+    // a tile's warp and block scans, |lo| stays within a few ulps of hi, and
+    // lo's own rounding is of order eps^2 |hi|)
+    __device__ static Acc combine_local(Acc a, Acc b) {
+        float s, e;
+        two_sum(a.x, b.x, s, e);
+        return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), e));
     }
+    // a thread-local run of outputs: it starts from the carry's lo (run_init)
+    // and sums its elements in plain fp32 on hi, and each output is the
+    // carry's hi plus the run: one add per element, as in the plain scan
+    __device__ static Acc run_init(Acc c) { return make_float2(c.y, 0.0f); }
+    __device__ static void accumulate(Acc& r, T x) { r.x = __fadd_rn(r.x, x); }
+    __device__ static T output(Acc c, Acc l) { return __fadd_rn(c.x, l.x); }
     __device__ static T output1(Acc v) { return __fadd_rn(v.x, v.y); }
     __device__ static Bits to_bits(Acc a) {
         return (static_cast<Bits>(__float_as_uint(a.y)) << 32) | __float_as_uint(a.x);
@@ -624,6 +636,46 @@ struct OpF32C {
                            __uint_as_float(static_cast<uint32_t>(b >> 32)));
     }
 };
+
+// The combine for the short dependent chains inside a tile (a thread's
+// sub-block sums and carries, warp scans, block carries): the operator's own
+// combine, unless the operator has a cheaper form for short chains
+// (compensated pairs: one TwoSum and no renormalisation).  Long chains (tile
+// and chunk prefixes, look-back folds, the scan of the tile sums across
+// blocks) keep the full combine.
+template <class Op, class = void>
+struct HasLocalCombine : std::false_type {};
+template <class Op>
+struct HasLocalCombine<Op, std::void_t<decltype(Op::combine_local(std::declval<typename Op::Acc>(),
+                                                                  std::declval<typename Op::Acc>()))>>
+    : std::true_type {};
+
+template <class Op>
+__device__ __forceinline__ typename Op::Acc combine_local(typename Op::Acc a, typename Op::Acc b) {
+    if constexpr (HasLocalCombine<Op>::value)
+        return Op::combine_local(a, b);
+    else
+        return Op::combine(a, b);
+}
+
+// The accumulator a thread's run of outputs starts from, given the carry c
+// into the run (everything before the run's first element): the identity,
+// unless the operator folds part of the carry into the run (compensated
+// pairs: c's lo, so that an output is c's hi plus the run).  Every
+// output(c, r) takes r from run_init(c) followed by accumulate steps.
+template <class Op, class = void>
+struct HasRunInit : std::false_type {};
+template <class Op>
+struct HasRunInit<Op, std::void_t<decltype(Op::run_init(std::declval<typename Op::Acc>()))>>
+    : std::true_type {};
+
+template <class Op>
+__device__ __forceinline__ typename Op::Acc run_init(typename Op::Acc c) {
+    if constexpr (HasRunInit<Op>::value)
+        return Op::run_init(c);
+    else
+        return Op::identity();
+}
 
 template <class Op>
 __device__ __forceinline__ typename Op::Acc shfl_up_acc(typename Op::Acc v, int d) {

@@ -254,12 +254,12 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < SUMU; ++u) v = Op::combine(v, part[u]);
+                for (int u = 0; u < SUMU; ++u) v = combine_local<Op>(v, part[u]);
             } else {
                 for (int i = lo + lane; i < hi; i += 32) Op::accumulate(v, buf[i]);
             }
 #pragma unroll
-            for (int d = 16; d >= 1; d >>= 1) v = Op::combine(v, shfl_down_acc<Op>(v, d));
+            for (int d = 16; d >= 1; d >>= 1) v = combine_local<Op>(v, shfl_down_acc<Op>(v, d));
             v = shfl_idx_acc<Op>(v, 0);
             if (lane == 0) publish_aggregate<Op>(p.rec, tile, epoch, cfg, f, v);
             bool ef;
@@ -362,13 +362,13 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
                     gf = f2;
                     gv = v2;
                 } else {
-                    gv = Op::combine(gv, c.wtot_v[w]);
+                    gv = combine_local<Op>(gv, c.wtot_v[w]);
                 }
             }
             if (HEADS != kNoHeads)
                 seg_combine<Op>(gf, gv, ef, ev);
             else
-                ev = Op::combine(gv, ev);
+                ev = combine_local<Op>(gv, ev);
             T y[ITEMS];
             thread_outputs_w<Op, ITEMS, HEADS>(x, hm, wh, ev, excl, y);
             store_items<T, ITEMS, TILE, REVERSE>(buf, tid, y);
@@ -531,17 +531,17 @@ __global__ void __launch_bounds__(THREADS) two_pass_kernel(const Params p) {
             if (warp == 0) {
                 Acc b = lane < NWARPS ? c.wtot_v[k & 1][lane] : Op::identity();
 #pragma unroll
-                for (int d = 16; d >= 1; d >>= 1) b = Op::combine(b, shfl_down_acc<Op>(b, d));
+                for (int d = 16; d >= 1; d >>= 1) b = combine_local<Op>(b, shfl_down_acc<Op>(b, d));
                 if (lane == 0) *rec_aux(p.rec, tile) = static_cast<unsigned long long>(Op::to_bits(b));
             }
             if (STAGES == 1) __syncthreads();
             continue;
         } else {
             Acc gv = Op::from_bits(static_cast<typename Op::Bits>(*rec_aux(p.rec, tile)));
-            for (int w = 0; w < warp; ++w) gv = Op::combine(gv, c.wtot_v[k & 1][w]);
+            for (int w = 0; w < warp; ++w) gv = combine_local<Op>(gv, c.wtot_v[k & 1][w]);
             Acc ev = shfl_up_acc<Op>(wv, 1);
             if (lane == 0) ev = Op::identity();
-            ev = Op::combine(gv, ev);
+            ev = combine_local<Op>(gv, ev);
             T y[ITEMS];
             thread_outputs<Op, ITEMS, kNoHeads>(x, 0u, ev, p.exclusive != 0, y);
             store_items<T, ITEMS, TILE, false>(buf, tid, y);
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(THREADS) scan_tile_sums_kernel(unsigned long l
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const Acc o = shfl_up_acc<Op>(inc, d);
-            if (lane >= d) inc = Op::combine(o, inc);
+            if (lane >= d) inc = combine_local<Op>(o, inc);
         }
         if (lane == 31) wsum[warp] = inc;
         __syncthreads();
@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(THREADS) scan_tile_sums_kernel(unsigned long l
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const Acc o = shfl_up_acc<Op>(w, d);
-                if (lane >= d) w = Op::combine(o, w);
+                if (lane >= d) w = combine_local<Op>(o, w);
             }
             Acc wx = shfl_up_acc<Op>(w, 1);
             if (lane == 0) wx = Op::identity();
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(THREADS) scan_tile_sums_kernel(unsigned long l
         __syncthreads();
         Acc ex = shfl_up_acc<Op>(inc, 1);
         if (lane == 0) ex = Op::identity();
-        ex = Op::combine(wsum[warp], ex);
+        ex = combine_local<Op>(wsum[warp], ex);
         ex = Op::combine(carry, ex);
         if (i < num_tiles) *rec_aux(rec, i) = static_cast<unsigned long long>(Op::to_bits(ex));
         carry = carry_s;

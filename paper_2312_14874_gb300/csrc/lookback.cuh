@@ -140,15 +140,15 @@ __device__ __forceinline__ typename Op::Acc stage_sum(const unsigned char* stage
                 Acc vs = Op::lift(e[0]);
 #pragma unroll
                 for (int j = 1; j < VEC; ++j) Op::accumulate(vs, e[j]);
-                part[u] = Op::combine(part[u], vs);
+                part[u] = combine_local<Op>(part[u], vs);
             }
         }
     }
     Acc v = part[0];
 #pragma unroll
-    for (int u = 1; u < U; ++u) v = Op::combine(v, part[u]);
+    for (int u = 1; u < U; ++u) v = combine_local<Op>(v, part[u]);
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) v = Op::combine(v, shfl_down_acc<Op>(v, d));
+    for (int d = 16; d >= 1; d >>= 1) v = combine_local<Op>(v, shfl_down_acc<Op>(v, d));
     return shfl_idx_acc<Op>(v, 0);
 }
 
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_scan_kernel(c
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
                     const Acc o = shfl_up_acc<Op>(inc, d);
-                    if (lane >= d) inc = Op::combine(o, inc);
+                    if (lane >= d) inc = combine_local<Op>(o, inc);
                 }
                 ex[j] = shfl_up_acc<Op>(inc, 1);
                 if (lane == 0) ex[j] = Op::identity();
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_scan_kernel(c
             }
             Acc wtot = rt[0];
 #pragma unroll
-            for (int j = 1; j < NV; ++j) wtot = Op::combine(wtot, rt[j]);
+            for (int j = 1; j < NV; ++j) wtot = combine_local<Op>(wtot, rt[j]);
             if (lane == 0) c.wtot[warp] = wtot;
             // warp totals exchanged; every consumer warp agrees on going on
             stop = named_barrier_or<NT>(1, stop);
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_scan_kernel(c
             Acc woff = Op::identity();
 #pragma unroll
             for (int w = 0; w < NW; ++w)
-                if (w < warp) woff = Op::combine(woff, c.wtot[w]);
+                if (w < warp) woff = combine_local<Op>(woff, c.wtot[w]);
             warp_spin_wait(&c.ready[s], use & 1u, role_limit, hdr, epoch, lane);
             Acc base = Op::combine(c.excl[s][use & 1u], woff);  // before the warp's first row
             named_barrier_sync<NT>(1);  // warp totals read before the next tile writes them
@@ -343,10 +343,10 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_scan_kernel(c
             const bool whole = p.fast && cnt == TILE;
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
-                const Acc carry = Op::combine(base, ex[j]);
-                base = Op::combine(base, rt[j]);
+                const Acc carry = combine_local<Op>(base, ex[j]);
+                base = combine_local<Op>(base, rt[j]);
                 T y[VEC];
-                Acc r = Op::identity();
+                Acc r = run_init<Op>(carry);
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) {
                     if (excl) {

@@ -537,7 +537,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     }
                 } else {
 #pragma unroll
-                    for (int d = 16; d >= 1; d >>= 1) wv = Op::combine(wv, shfl_down_acc<Op>(wv, d));
+                    for (int d = 16; d >= 1; d >>= 1) wv = combine_local<Op>(wv, shfl_down_acc<Op>(wv, d));
                     if (lane == 0) c.wtot_v[warp] = wv;
                 }
                 named_barrier_sync<CTHREADS>(1);
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                             total_f = f2;
                             total = v2;
                         } else {
-                            total = Op::combine(total, wt[w]);
+                            total = combine_local<Op>(total, wt[w]);
                         }
                     }
                     publish_sum_hooked<Op>(p.rec, t, epoch, cfg, total_f, total);
@@ -654,13 +654,13 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                 if (w < warp) {
                     if constexpr (HEADS != kNoHeads) {
                         if (wtf[w] != 0u) gv = wt[w];
-                        else gv = Op::combine(gv, wt[w]);
+                        else gv = combine_local<Op>(gv, wt[w]);
                     } else {
-                        gv = Op::combine(gv, wt[w]);
+                        gv = combine_local<Op>(gv, wt[w]);
                     }
                 }
             }
-            if (!xf) ev = Op::combine(gv, ev);
+            if (!xf) ev = combine_local<Op>(gv, ev);
             T y[ITEMS];
             thread_outputs_w<Op, ITEMS, HEADS>(x, hm, wh, ev, excl, y);
             store_items<T, ITEMS, TILE, false>(buf, tid, y);

@@ -82,7 +82,7 @@ __device__ __forceinline__ typename Op::Acc resident_prefix(unsigned long long* 
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (st[q] != kStateX) {
-                    s = Op::combine(s, v[q]);
+                    s = combine_local<Op>(s, v[q]);
                     pending &= ~(1u << (k0 + q));
                 }
             }
@@ -105,7 +105,7 @@ __device__ __forceinline__ typename Op::Acc resident_prefix(unsigned long long* 
         poll_round_fence();
     }
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) s = Op::combine(s, shfl_xor_acc<Op>(s, d));
+    for (int d = 16; d >= 1; d >>= 1) s = combine_local<Op>(s, shfl_xor_acc<Op>(s, d));
     return s;
 }
 
@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(THREADS, MINB) resident_scan_kernel(const Para
 #pragma unroll
     for (int w = 0; w < NWARPS; ++w) {
         const Acc wt = c.wtot[w];
-        agg = Op::combine(agg, wt);
-        if (w < warp) woff = Op::combine(woff, wt);
+        agg = combine_local<Op>(agg, wt);
+        if (w < warp) woff = combine_local<Op>(woff, wt);
     }
 
     // ---- the tile's sum out, the sums of the tiles before it in ----------

@@ -107,7 +107,7 @@ __device__ __forceinline__ void thread_reduce(const typename Op::T (&x)[ITEMS], 
         split_sums<Op, ITEMS>(x, part);
         v = part[0];
 #pragma unroll
-        for (int k = 1; k < Op::kSplit; ++k) v = Op::combine(v, part[k]);
+        for (int k = 1; k < Op::kSplit; ++k) v = combine_local<Op>(v, part[k]);
         return;
     }
     v = Op::identity();
@@ -138,14 +138,14 @@ __device__ __forceinline__ void warp_inclusive_scan(bool& f, typename Op::Acc& v
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const Acc vo = shfl_up_acc<Op>(v, d);
-            if (lane - d >= start) v = Op::combine(vo, v);
+            if (lane - d >= start) v = combine_local<Op>(vo, v);
         }
         f = upto != 0u;
     } else {
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const Acc vo = shfl_up_acc<Op>(v, d);
-            if (lane >= d) v = Op::combine(vo, v);
+            if (lane >= d) v = combine_local<Op>(vo, v);
         }
     }
 }
@@ -168,10 +168,10 @@ __device__ __forceinline__ void thread_outputs_t(const typename Op::T (&x)[ITEMS
         Acc cin[K];
         cin[0] = gv;
 #pragma unroll
-        for (int k = 1; k < K; ++k) cin[k] = Op::combine(cin[k - 1], part[k - 1]);
+        for (int k = 1; k < K; ++k) cin[k] = combine_local<Op>(cin[k - 1], part[k - 1]);
         Acc r[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) r[k] = Op::identity();
+        for (int k = 0; k < K; ++k) r[k] = run_init<Op>(cin[k]);
 #pragma unroll
         for (int j = 0; j < L; ++j) {
 #pragma unroll
@@ -184,7 +184,7 @@ __device__ __forceinline__ void thread_outputs_t(const typename Op::T (&x)[ITEMS
         return;
     }
     bool rf = false;
-    Acc rv = Op::identity();
+    Acc rv = run_init<Op>(gv);
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const bool h = HEADS != kNoHeads && ((hm >> j) & 1u);
