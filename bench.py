@@ -15,8 +15,9 @@ end-to-end number through the public API with host buffers, next to a
 copy-only run of the same host-link schedule; SM clocks sampled during the
 timed region; the CPU oracle timed on a bounded sample (cpu_baseline); and
 side measurements of the other kernels (single-pass, two-pass, int64, fp32
-plain and compensated, segmented, row-wise forward/backward, compaction,
-device copy) at their own sizes.
+plain and compensated, the small-input resident scan at int32 2^20 with the
+L2 flushed, segmented, row-wise forward/backward, compaction, device copy) at
+their own sizes.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --profile-case scan|seg_f32|compact_i32 ...   (profiler target)
@@ -58,7 +59,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-side", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--algo", choices=["auto", "single_pass", "two_pass", "partitioned"],
+    ap.add_argument("--algo", choices=["auto", "single_pass", "two_pass", "partitioned", "resident"],
                     default="auto", help="scan algorithm of the timed step (auto: the tuned "
                     "fastest algorithm and variant for this GPU and size)")
     ap.add_argument("--n-log2", type=int, default=N_LOG2,
@@ -219,9 +220,11 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def cuda_time_ms(fn, reps: int, flush=None) -> tuple[float, float]:
-    """(median, min) ms of fn over reps, CUDA events on the current stream;
-    flush() runs between reps outside the timed interval."""
+def cuda_time_ms(fn, reps: int, flush=None) -> tuple[float, float, float]:
+    """(median, min, mean) ms of fn over reps, CUDA events on the current
+    stream; flush() runs between reps outside the timed interval.  Events tick
+    in steps of about 2 us on GB300, so for microsecond kernels the mean of
+    many reps resolves what the median cannot."""
     import torch
     s = torch.cuda.current_stream()
     times = []
@@ -235,7 +238,7 @@ def cuda_time_ms(fn, reps: int, flush=None) -> tuple[float, float]:
         b.record(s)
         b.synchronize()
         times.append(a.elapsed_time(b))
-    return statistics.median(times), min(times)
+    return statistics.median(times), min(times), statistics.mean(times)
 
 
 # ---- CPU oracle baseline ------------------------------------------------------
@@ -369,10 +372,18 @@ def side_measurements(dev, peak) -> dict:
     x1 = torch.randint(0, 16, (n1,), dtype=torch.int32, device=dev)
     y1 = torch.empty_like(x1)
     flush_small = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    ms1 = cuda_time_ms(lambda: gb.inclusive(x1, out=y1, workspace=ws), reps,
-                       lambda: flush_small.fill_(1))[0]
-    rec("i32_2^20_flushed", 8 * n1, ms1)
-    res["i32_2^20_flushed"]["us"] = round(ms1 * 1e3, 2)
+    med1, _, mean1 = cuda_time_ms(lambda: gb.inclusive(x1, out=y1, workspace=ws), 200,
+                                  lambda: flush_small.fill_(1))
+    rec("i32_2^20_flushed", 8 * n1, mean1)
+    res["i32_2^20_flushed"]["us"] = round(mean1 * 1e3, 2)
+    res["i32_2^20_flushed"]["us_median"] = round(med1 * 1e3, 2)
+    res["i32_2^20_flushed"]["algo"] = "auto: " + ":".join(str(v) for v in autotune.choose("scan_i32", "i32", n1, "auto"))
+    # the persistent single-pass kernel at the same size, for comparison
+    v1 = pick("scan_i32", n1, "single_pass")
+    mean_sp = cuda_time_ms(lambda: gb.inclusive(x1, out=y1, workspace=ws, algo="single_pass", variant=v1),
+                           200, lambda: flush_small.fill_(1))[2]
+    rec("i32_2^20_flushed_single_pass", 8 * n1, mean_sp)
+    res["i32_2^20_flushed_single_pass"]["us"] = round(mean_sp * 1e3, 2)
     del x1, y1, flush_small
     # fp32 2^28, plain and compensated
     nf = 1 << 28

@@ -6,13 +6,16 @@
  * is y_k = a_0 + ... + a_k; the exclusive scan is y_0 = 0, y_k = a_0 + ... +
  * a_{k-1}.  The paper's algorithms are multithreaded two-pass CPU schemes
  * (Section 2.1, Figure 1) and in-register SIMD scans (Section 3, Listing 1);
- * this library computes the same result on the GPU with three algorithms a
+ * this library computes the same result on the GPU with four algorithms a
  * caller can pick (gbscan_algo): a single-pass chained scan with decoupled
  * look-back; the two-pass reduce-then-scan (the paper's "Accumulate + Prefix
- * Sum", Figure 1b); and the partitioned scan (Section 2.2, Figure 2) with the
- * GPU's L2 as the cache, whose second pass over each chunk reads it from L2.
- * GBSCAN_ALGO_AUTO takes the partitioned scan for large 4-byte arrays and the
- * single-pass scan for smaller ones and for int64 (see the plain scans).
+ * Sum", Figure 1b); the partitioned scan (Section 2.2, Figure 2) with the
+ * GPU's L2 as the cache, whose second pass over each chunk reads it from L2;
+ * and, for inputs whose tiles all fit the SMs at once, the resident scan: the
+ * same two passes with the whole array held in shared memory, one launch.
+ * GBSCAN_ALGO_AUTO takes the resident scan where it fits, the partitioned
+ * scan for large 4-byte arrays and the single-pass scan for the sizes
+ * between and for int64 (see the plain scans).
  *
  * Conventions for every entry point:
  *  - Pointers named in/out/offsets/grad_* and the workspace are DEVICE
