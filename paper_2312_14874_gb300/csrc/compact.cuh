@@ -121,8 +121,25 @@ constexpr int cp_smem_bytes() {
     return STAGES * CWARPS * 32 * ITEMS * 5 + static_cast<int>(sizeof(CpCtrl<CWARPS, STAGES>));
 }
 
-// Nonzero bytes among the thread's ITEMS flags (ITEMS a multiple of 4; the flag
-// run starts 4-byte aligned).
+// The number of nonzero bytes among the thread's ITEMS flags, four at a time
+// (each byte's bits ORed down into its bit 0; ITEMS a multiple of 4, the flag
+// run 4-byte aligned).
+template <int ITEMS>
+__device__ __forceinline__ uint32_t keep_count(const uint8_t* f) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(f);
+    uint32_t n = 0;
+#pragma unroll
+    for (int q = 0; q < ITEMS / 4; ++q) {
+        uint32_t t = w[q];
+        t |= t >> 4;
+        t |= t >> 2;
+        t |= t >> 1;
+        n += __popc(t & 0x01010101u);
+    }
+    return n;
+}
+
+// Bit j set: the thread's flag j is nonzero.
 template <int ITEMS>
 __device__ __forceinline__ uint32_t keep_mask(const uint8_t* f) {
     static_assert(ITEMS % 4 == 0 && ITEMS <= 32, "whole flag words, one 32-bit mask");
@@ -130,10 +147,15 @@ __device__ __forceinline__ uint32_t keep_mask(const uint8_t* f) {
     uint32_t m = 0;
 #pragma unroll
     for (int q = 0; q < ITEMS / 4; ++q) {
-        const uint32_t v = w[q];
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-            if ((v >> (8 * b)) & 0xffu) m |= 1u << (4 * q + b);
+        // bit 0 of each byte: the byte is nonzero (its bits ORed down), then
+        // the multiply gathers the four bits 0, 8, 16, 24 into bits 24..27
+        // (each product term lands on its own bit: no carries reach them)
+        uint32_t t = w[q];
+        t |= t >> 4;
+        t |= t >> 2;
+        t |= t >> 1;
+        t &= 0x01010101u;
+        m |= ((t * 0x01020408u) >> 24) << (4 * q);
     }
     return m;
 }
@@ -317,19 +339,32 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             if (phase == kItemReduce) {
                 // ---- R item: the kept counts of the group's tiles ------------
                 const uint8_t* fb = reinterpret_cast<const uint8_t*>(payload(s));
+                // the thread's kept counts of the four tiles (at most ITEMS
+                // each, a warp's at most 640), two to a word, so that the warp
+                // sums take two shuffle reductions instead of four
+                uint32_t packed[kCpGroup / 2] = {};
 #pragma unroll
                 for (int g = 0; g < kCpGroup; ++g) {
                     const int64_t tg = t * kCpGroup + g;
                     const int cg = tg < num_tiles ? count_of(tg) : 0;
-                    uint32_t mg = 0;
-                    if (cg > 0) {
-                        mg = keep_mask<ITEMS>(fb + g * TILE + tid * ITEMS);
-                        if (cg < TILE) mg &= valid_items<ITEMS>(cg, tid);
+                    uint32_t v = 0;
+                    if (cg == TILE) {
+                        v = keep_count<ITEMS>(fb + g * TILE + tid * ITEMS);
+                    } else if (cg > 0) {
+                        v = __popc(keep_mask<ITEMS>(fb + g * TILE + tid * ITEMS) & valid_items<ITEMS>(cg, tid));
                     }
-                    uint32_t v = __popc(mg);
+                    packed[g / 2] |= v << (16 * (g & 1));
+                }
+                static_assert(kCpGroup % 2 == 0 && 32 * ITEMS < 65536, "two warp counts fit one word");
+#pragma unroll
+                for (int q = 0; q < kCpGroup / 2; ++q) {
+                    uint32_t v = packed[q];
 #pragma unroll
                     for (int d = 16; d >= 1; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
-                    if (lane == 0) c.gtot[g][warp] = v;
+                    if (lane == 0) {
+                        c.gtot[2 * q][warp] = v & 0xffffu;
+                        c.gtot[2 * q + 1][warp] = v >> 16;
+                    }
                 }
                 named_barrier_sync<CTHREADS>(1);  // group counts written, flags read
                 if (tid == 0) {
@@ -391,14 +426,17 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             const unsigned long long base = c.base;
             const uint32_t shift = static_cast<uint32_t>(base & 3ull);
             uint32_t pos = shift + inc - mine;  // this thread's first stage index
-            for (int w = 0; w < warp; ++w) pos += static_cast<uint32_t>(c.wtot[w]);
+#pragma unroll
+            for (int w = 0; w < CWARPS; ++w)
+                if (w < warp) pos += static_cast<uint32_t>(c.wtot[w]);
+            // pos + the thread's kept count <= shift + the tile's kept count
+            // <= 3 + TILE: every counted flag is one of this tile's
             T* xb = payload(s);
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if ((m >> j) & 1u) {
-                    if (pos < static_cast<uint32_t>(TILE) + 3u) xb[pos] = x[j];
-                    ++pos;
-                }
+            for (int j = 0; j < ITEMS; ++j) {
+                if ((m >> j) & 1u) xb[pos] = x[j];
+                pos += (m >> j) & 1u;
+            }
             named_barrier_sync<CTHREADS>(1);  // the run is gathered; kept is set
             uint32_t kept = c.kept;
             // a run that would leave the output (only after a failed wait, which
