@@ -103,10 +103,9 @@ struct CpCtrl {
     int64_t tile_id[STAGES];
     uint32_t phase[STAGES];
     alignas(16) unsigned long long stat[STAGES][6];
-    unsigned long long wtot[CWARPS];
+    uint32_t wtot[CWARPS];    // S item: the warps' kept counts
     uint32_t gtot[kCpGroup][CWARPS];  // R item: per tile of the group, the warps' counts
     unsigned long long base;  // S item: the output position of the tile's first kept element
-    uint32_t kept;            // S item: the tile's kept count
     uint64_t scan_req;
     uint64_t scan_idle;
     int64_t scan_chunk;
@@ -413,11 +412,6 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             load_items<T, ITEMS, TILE, false>(payload(s), tid, x);
             named_barrier_sync<CTHREADS>(1);  // warp totals written, payload read
             // ---- scan item: positions of the kept elements, gather, write --
-            if (tid == 0) {
-                uint32_t total = 0;
-                for (int w = 0; w < CWARPS; ++w) total += static_cast<uint32_t>(c.wtot[w]);
-                c.kept = total;
-            }
             // The run is gathered at stage index shift + (position in the run),
             // shift = base mod 4, so that stage index i and output element
             // base - shift + i share their 16-byte alignment; the up to three
@@ -426,9 +420,13 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
             const unsigned long long base = c.base;
             const uint32_t shift = static_cast<uint32_t>(base & 3ull);
             uint32_t pos = shift + inc - mine;  // this thread's first stage index
+            uint32_t kept = 0;                  // the tile's kept count
 #pragma unroll
-            for (int w = 0; w < CWARPS; ++w)
-                if (w < warp) pos += static_cast<uint32_t>(c.wtot[w]);
+            for (int w = 0; w < CWARPS; ++w) {
+                const uint32_t wt = c.wtot[w];
+                kept += wt;
+                if (w < warp) pos += wt;
+            }
             // pos + the thread's kept count <= shift + the tile's kept count
             // <= 3 + TILE: every counted flag is one of this tile's
             T* xb = payload(s);
@@ -437,8 +435,7 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                 if ((m >> j) & 1u) xb[pos] = x[j];
                 pos += (m >> j) & 1u;
             }
-            named_barrier_sync<CTHREADS>(1);  // the run is gathered; kept is set
-            uint32_t kept = c.kept;
+            named_barrier_sync<CTHREADS>(1);  // the run is gathered
             // a run that would leave the output (only after a failed wait, which
             // has recorded its error) is not written
             if (kept > static_cast<uint32_t>(TILE) || base > static_cast<unsigned long long>(p.n) ||
