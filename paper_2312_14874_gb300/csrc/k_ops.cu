@@ -23,12 +23,13 @@ GBSCAN_OP_FAMILY(family_max_f32, OpMaxF32)
 GBSCAN_OP_FAMILY(family_min_f32, OpMinF32)
 
 static const Variant kCompact[] = {
-    GBSCAN_VARIANT_COMPACT(8, 20, 4, 2),
     GBSCAN_VARIANT_COMPACT(8, 20, 3, 2),
+    GBSCAN_VARIANT_COMPACT(16, 28, 2, 1),
+    GBSCAN_VARIANT_COMPACT(8, 28, 3, 2),
 };
 
 const Family& family_compact() {
-    static const Family f{2, kCompact, nullptr};
+    static const Family f{3, kCompact, nullptr};
     return f;
 }
 
