@@ -2,9 +2,9 @@
 [0, 255] (seed 0), on one GB300.
 
 One step = one scan of the whole 2^30-element array with the algorithm and
-launch shape the autotuner picked for this GPU and size (the partitioned
-scan at 2^30: one persistent launch per step), tile load through carry add
-and store.  The metric is GB/s = (bytes read + bytes written) / device time,
+launch shape the autotuner picked for this GPU and size (the single-pass
+chained scan with decoupled look-back at 2^30: one persistent launch per
+step), tile load through carry add and store.  The metric is GB/s = (bytes read + bytes written) / device time,
 with 8 * 2^30 bytes per step; inputs (4 GiB) and outputs are larger than the
 129 MB L2, so no flush is needed between steps.
 
@@ -560,8 +560,8 @@ def main(argv=None) -> int:
     y = torch.empty_like(x)
     ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_SCAN, N), dev)
     algo, variant = autotune.choose("scan_i32", "i32", N, args.algo)
-    if algo == "auto":  # no tuned table: the library's own rule, spelled out
-        algo = "partitioned" if 4 * N >= (128 << 20) else "two_pass"
+    if algo == "auto":  # no tuned table: the library's own rule at this size, spelled out
+        algo = "single_pass"
     launches_per_step = 3 if algo == "two_pass" else 1
     stream = torch.cuda.current_stream(dev)
 
@@ -746,14 +746,16 @@ def main(argv=None) -> int:
     return 0
 
 
-# The sources the timed int32 partitioned kernel is built and launched from:
-# its template and the tile code it uses, the shared device definitions, the
-# launcher, the int32 variant table, the host dispatch and the C header.  The
-# other kernels' sources (single-pass, two-pass, row-block, compaction) do not
-# change its code.
+# The sources the timed int32 kernel (the single-pass look-back kernel, or the
+# partitioned one when a tuned table picks it) is built and launched from:
+# their templates and the tile code they use, the shared device definitions,
+# the launcher, the int32 variant table, the host dispatch and the C header.
+# The other kernels' sources (two-pass, resident, row-block, compaction) do
+# not change their code.
 STAMP_SOURCES = ("include/gbscan.h",
                  "paper_2312_14874_gb300/csrc/gbscan_device.cuh",
                  "paper_2312_14874_gb300/csrc/tile_common.cuh",
+                 "paper_2312_14874_gb300/csrc/lookback.cuh",
                  "paper_2312_14874_gb300/csrc/partitioned.cuh",
                  "paper_2312_14874_gb300/csrc/gbscan_launch.cuh",
                  "paper_2312_14874_gb300/csrc/k_i32.cu",

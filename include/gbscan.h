@@ -13,9 +13,8 @@
  * GPU's L2 as the cache, whose second pass over each chunk reads it from L2;
  * and, for inputs whose tiles all fit the SMs at once, the resident scan: the
  * same two passes with the whole array held in shared memory, one launch.
- * GBSCAN_ALGO_AUTO takes the resident scan where it fits, the partitioned
- * scan for large 4-byte arrays and the single-pass scan for the sizes
- * between and for int64 (see the plain scans).
+ * GBSCAN_ALGO_AUTO takes the resident scan where it fits and the single-pass
+ * scan above that (see the plain scans).
  *
  * Conventions for every entry point:
  *  - Pointers named in/out/offsets/grad_* and the workspace are DEVICE
@@ -130,9 +129,10 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
  *               after a grid-wide barrier adds the sums of the tiles before it; for
  *               inputs of at most SMs x blocks-per-SM tiles, gbscan_resident_max_n;
  *               larger inputs return GBSCAN_ERR_UNSUPPORTED), or AUTO (RESIDENT where it fits;
- *               above that, 4-byte elements: PARTITIONED for inputs of 128 MiB or more,
- *               SINGLE_PASS below; int64: SINGLE_PASS; compensated fp32 and fp64:
- *               TWO_PASS; the fastest choices measured on GB300).
+ *               above that SINGLE_PASS, except compensated fp32 and fp64: TWO_PASS; the
+ *               fastest choices measured on GB300).  SINGLE_PASS and PARTITIONED prefetch
+ *               the input into L2 about 12 MiB ahead of their tile copies (environment
+ *               variable GBSCAN_PREFETCH_BYTES; 1 turns it off).
  *   variant   : launch shape (threads, items per thread, pipeline stages), 0 = default;
  *               see gbscan_num_variants / gbscan_variant_info.  RESIDENT has one shape:
  *               the variant is checked but does not change the launch.

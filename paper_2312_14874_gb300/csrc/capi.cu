@@ -231,13 +231,12 @@ static long long env_cached(std::atomic<long long>& cache, const char* name, lon
     return v;
 }
 
-// GBSCAN_ALGO_AUTO: 4-byte elements take the partitioned scan from this input
-// size on and the single-pass scan (one launch) below it; 8-byte elements take
-// the single-pass scan at every size (measured on GB300: int64 single-pass is
-// the fastest from 2^24 to 2^30 elements).  Compensated fp32 and fp64, whose
-// scans are bound by arithmetic (TwoSum pairs; fp64 adds), take the two-pass
-// scan (their entry points decide that before calling scan_flat).
-constexpr uint64_t kAutoPartitionedBytes = 128ull << 20;
+// GBSCAN_ALGO_AUTO: the resident scan wherever it fits; above that the
+// single-pass scan (measured on GB300 with the L2 prefetch ahead of each
+// claim: the fastest of the four for int32, fp32 and int64 from 2^24 to 2^30
+// elements).  Compensated fp32 and fp64, whose scans are bound by arithmetic
+// (TwoSum pairs; fp64 adds), take the two-pass scan above the resident size
+// (their entry points decide that before calling scan_flat).
 
 int64_t partition_chunk_tiles(const Variant& v, size_t esz) {
     static std::atomic<long long> bytes_cache{0};
@@ -271,6 +270,20 @@ gbscan_algo auto_arith_bound(const Family& fam, int64_t n, gbscan_algo algo) {
     return resident_fits(fam, n) ? GBSCAN_ALGO_RESIDENT : GBSCAN_ALGO_TWO_PASS;
 }
 
+// Single-pass scan: how far ahead of each claim the loader prefetches a tile
+// into L2, in bytes of input (GBSCAN_PREFETCH_BYTES, default 12 MiB; 1 turns
+// the prefetch off).  Measured on GB300 at int32 2^30 with 28 KB tiles: 0.80
+// of a device copy without it, 0.92 at 7-14 MiB ahead; at 56 MiB the
+// prefetched lines start to leave L2 before their copy.
+constexpr long long kDefaultPrefetchBytes = 12ll << 20;
+
+int64_t single_pass_prefetch_tiles(int tile, size_t esz) {
+    static std::atomic<long long> cache{0};
+    const long long bytes = env_cached(cache, "GBSCAN_PREFETCH_BYTES", kDefaultPrefetchBytes);
+    const long long tile_bytes = static_cast<long long>(tile) * static_cast<long long>(esz);
+    return bytes > tile_bytes ? bytes / tile_bytes : 0;
+}
+
 gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n, size_t esz,
                         int exclusive, void* ws, size_t ws_bytes, gbscan_algo algo, int variant,
                         cudaStream_t stream) {
@@ -285,13 +298,7 @@ gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n,
     if (st != GBSCAN_OK) return st;
     const Variant& v = fam.variants[variant];
     if (algo == GBSCAN_ALGO_AUTO) {
-        if (resident_fits(fam, n))
-            algo = GBSCAN_ALGO_RESIDENT;
-        else if (esz == 4 && v.partitioned &&
-                 static_cast<uint64_t>(n) * esz >= kAutoPartitionedBytes)
-            algo = GBSCAN_ALGO_PARTITIONED;
-        else
-            algo = GBSCAN_ALGO_SINGLE_PASS;
+        algo = resident_fits(fam, n) ? GBSCAN_ALGO_RESIDENT : GBSCAN_ALGO_SINGLE_PASS;
     }
     if (algo == GBSCAN_ALGO_RESIDENT && !resident_fits(fam, n)) return GBSCAN_ERR_UNSUPPORTED;
     const int tile = algo == GBSCAN_ALGO_RESIDENT ? fam.resident_tile : v.tile;
@@ -306,6 +313,7 @@ gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n,
         if (!v.partitioned) return GBSCAN_ERR_UNSUPPORTED;
         p.chunk_tiles = partition_chunk_tiles(v, esz);
         p.chunk_lag = partition_chunk_lag();
+        p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, esz);
         return from_cuda(v.partitioned(p, stream));
     }
     if (algo == GBSCAN_ALGO_TWO_PASS) {
@@ -315,6 +323,7 @@ gbscan_status scan_flat(const Family& fam, const void* in, void* out, int64_t n,
         if (e == cudaSuccess) e = v.scan_offset(p, stream);
         return from_cuda(e);
     }
+    p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, esz);
     return from_cuda(v.single_pass(p, stream));
 }
 

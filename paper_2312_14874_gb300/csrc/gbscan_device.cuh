@@ -128,6 +128,8 @@ struct Params {
     const uint8_t* flags;   // compaction: keep flags (nonzero = keep)
     unsigned long long* total_out; // compaction: the number kept (the last chunk prefix), or null
     const void* carry_in;   // partitioned scan: one element (device) folded in before element 0, or null
+    int64_t prefetch_tiles; // single-pass scan: the loader asks L2 for the tile this far ahead of
+                            // each claim (0: no prefetch)
     int exclusive;
     int fast;               // in and out are 16-byte aligned: TMA path for full tiles
 };
@@ -217,6 +219,12 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     return pol;
+}
+
+// Asks L2 to fetch `bytes` bytes at `src` (16-byte aligned, a multiple of 16
+// bytes); nothing waits for it.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void bulk_load_hint(void* dst_smem, const void* src, uint32_t bytes,

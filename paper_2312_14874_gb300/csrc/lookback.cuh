@@ -244,6 +244,15 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_scan_kernel(c
                     c.tile_id[s] = tile;
                     mbar_arrive_expect_tx(&c.full[s], TILE_BYTES);
                     bulk_load_hint(buf, in + tile * TILE, TILE_BYTES, &c.full[s], evict_first);
+                    // the tile prefetch_tiles ahead, into L2 for whichever block
+                    // claims it: its copy then comes from L2 (no claim is made,
+                    // so no tile's aggregate is delayed)
+                    const int64_t pt = tile + p.prefetch_tiles;
+                    if (p.prefetch_tiles > 0 && pt < num_tiles) {
+                        const uint32_t pbytes =
+                            (static_cast<uint32_t>(count_of(pt)) * static_cast<uint32_t>(sizeof(T))) & ~15u;
+                        if (pbytes) bulk_prefetch_l2(in + pt * TILE, pbytes);
+                    }
                 }
             } else {
                 // ragged or misaligned: the aligned body by one bulk copy where

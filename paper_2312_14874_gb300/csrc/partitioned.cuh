@@ -438,6 +438,15 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) partitioned_kernel(co
                     if (body)
                         bulk_load_hint(buf, in + t * TILE, body, &c.full[s],
                                        phase == kItemReduce ? keep : drop);
+                    // a reduce item's copy is the tile's first read: the tile
+                    // prefetch_tiles ahead goes to L2 now, so that its reduce
+                    // item's copy comes from L2 (no item is claimed for it)
+                    const int64_t pt = t + p.prefetch_tiles;
+                    if (phase == kItemReduce && p.prefetch_tiles > 0 && p.fast && pt < num_tiles) {
+                        const uint32_t pbytes =
+                            (static_cast<uint32_t>(count_of(pt)) * static_cast<uint32_t>(sizeof(T))) & ~15u;
+                        if (pbytes) bulk_prefetch_l2(in + pt * TILE, pbytes);
+                    }
                     if constexpr (HEADS != kNoHeads)
                         bulk_load(&c.bits[s][0], p.bitmap + t * (TILE / 32), BITS_BYTES, &c.full[s]);
                     if (stat_bytes) {
