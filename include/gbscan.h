@@ -130,9 +130,9 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
  *               inputs of at most SMs x blocks-per-SM tiles, gbscan_resident_max_n;
  *               larger inputs return GBSCAN_ERR_UNSUPPORTED), or AUTO (RESIDENT where it fits;
  *               above that SINGLE_PASS, except compensated fp32 and fp64: TWO_PASS; the
- *               fastest choices measured on GB300).  SINGLE_PASS and PARTITIONED prefetch
- *               the input into L2 about 12 MiB ahead of their tile copies (environment
- *               variable GBSCAN_PREFETCH_BYTES; 1 turns it off).
+ *               fastest choices measured on GB300).  SINGLE_PASS and PARTITIONED (and
+ *               stream compaction) prefetch the input into L2 about 12 MiB ahead of their
+ *               tile copies (environment variable GBSCAN_PREFETCH_BYTES; 1 turns it off).
  *   variant   : launch shape (threads, items per thread, pipeline stages), 0 = default;
  *               see gbscan_num_variants / gbscan_variant_info.  RESIDENT has one shape:
  *               the variant is checked but does not change the launch.

@@ -270,11 +270,14 @@ gbscan_algo auto_arith_bound(const Family& fam, int64_t n, gbscan_algo algo) {
     return resident_fits(fam, n) ? GBSCAN_ALGO_RESIDENT : GBSCAN_ALGO_TWO_PASS;
 }
 
-// Single-pass scan: how far ahead of each claim the loader prefetches a tile
-// into L2, in bytes of input (GBSCAN_PREFETCH_BYTES, default 12 MiB; 1 turns
-// the prefetch off).  Measured on GB300 at int32 2^30 with 28 KB tiles: 0.80
-// of a device copy without it, 0.92 at 7-14 MiB ahead; at 56 MiB the
-// prefetched lines start to leave L2 before their copy.
+// Single-pass, partitioned and compaction scans: how far ahead of each claim
+// the loader prefetches a tile into L2, in bytes of input
+// (GBSCAN_PREFETCH_BYTES, default 12 MiB; 1 turns the prefetch off).
+// Measured on GB300 at int32 2^30 with 28 KB tiles, single-pass: 0.80 of a
+// device copy without it, 0.92 at 7-14 MiB ahead; at 56 MiB the prefetched
+// lines start to leave L2 before their copy.  The two-pass kernels take no
+// prefetch: their static schedule already keeps several grid-wide steps of
+// copies in flight, and a prefetch only added requests (0.57 -> 0.53).
 constexpr long long kDefaultPrefetchBytes = 12ll << 20;
 
 int64_t single_pass_prefetch_tiles(int tile, size_t esz) {
@@ -389,6 +392,7 @@ gbscan_status scan_seg_impl(const Family& fam, const void* in, void* out, int64_
         p.bitmap = bitmap;
         p.chunk_tiles = partition_chunk_tiles(v, esz);
         p.chunk_lag = partition_chunk_lag();
+        p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, esz);
         return from_cuda(v.partitioned(p, stream));
     }
     // each tile's first segment for the single-pass kernel (also checks the
@@ -422,6 +426,7 @@ gbscan_status compact_impl(const void* in, const uint8_t* flags, void* out, int6
     // whole R groups per chunk
     p.chunk_tiles = (partition_chunk_tiles(v, 4) + kCpGroup - 1) / kCpGroup * kCpGroup;
     p.chunk_lag = partition_chunk_lag();
+    p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, 4);
     return from_cuda(v.partitioned(p, stream));
 }
 
@@ -617,6 +622,7 @@ gbscan_status scan_inclusive_i32_host(const int32_t* h_in, int32_t* h_out, int64
             Params p = make_params(slot, slot, len, v.tile, ws, ws_bytes);
             p.chunk_tiles = partition_chunk_tiles(v, 4);
             p.chunk_lag = partition_chunk_lag();
+            p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, 4);
             p.carry_in = k > 0 ? &hdr->host_carry : nullptr;
             e = v.partitioned(p, s_cmp);
         }

@@ -280,6 +280,25 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
                     if (fbytes)
                         bulk_load_hint(fb, fl + f0, fbytes, &c.full[s], phase == kItemReduce ? keep : drop);
                     if (xbytes) bulk_load_hint(xb, in + t * TILE, xbytes, &c.full[s], drop);
+                    // the first DRAM reads (an S item's payload, an R item's
+                    // flags) of the item prefetch_tiles tiles ahead go to L2 now,
+                    // so that its copy comes from L2 (no item is claimed for it)
+                    if (p.prefetch_tiles > 0) {
+                        if (phase == kItemScan && p.fast) {
+                            const int64_t pt = t + p.prefetch_tiles;
+                            if (pt < num_tiles) {
+                                const uint32_t pb = (static_cast<uint32_t>(count_of(pt)) * 4u) & ~15u;
+                                if (pb) bulk_prefetch_l2(in + pt * TILE, pb);
+                            }
+                        } else if (phase == kItemReduce && (reinterpret_cast<uintptr_t>(fl) & 15) == 0) {
+                            const int64_t pf0 = f0 + p.prefetch_tiles * static_cast<int64_t>(TILE);
+                            if (pf0 < p.n) {
+                                const int64_t rem = p.n - pf0;
+                                const uint32_t pb = static_cast<uint32_t>(rem < fcap ? rem : fcap) & ~15u;
+                                if (pb) bulk_prefetch_l2(fl + pf0, pb);
+                            }
+                        }
+                    }
                     if (stat_bytes) {
                         // the tile's status pair and the chunk's E pair
                         bulk_load(&c.stat[s][0], rec_tile<OpI64>(p.rec, t), 16, &c.full[s]);
