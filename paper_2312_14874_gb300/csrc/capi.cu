@@ -349,6 +349,7 @@ gbscan_status scan_rows_impl(const Family& fam, const void* in, void* out, int64
     p.cols = cols;
     cudaGetLastError();
     if (v.rowblock && cols <= v.rowblock_tile) return from_cuda(v.rowblock(p, stream));
+    p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, esz);
     return from_cuda(v.single_pass(p, stream));
 }
 
@@ -401,6 +402,7 @@ gbscan_status scan_seg_impl(const Family& fam, const void* in, void* out, int64_
         offsets, num_segments, n, v.tile, p.num_tiles, p.rec, p.hdr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return GBSCAN_ERR_CUDA;
+    p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, esz);
     return from_cuda(v.single_pass(p, stream));
 }
 

@@ -155,6 +155,15 @@ __global__ void __launch_bounds__((CWARPS + 1 + STAGES) * 32, MINB) ws_scan_kern
                     c.tile_id[s] = tile;
                     mbar_arrive_expect_tx(&c.full[s], TILE_BYTES);
                     bulk_load(buf, in + tb, TILE_BYTES, &c.full[s]);
+                    // the tile prefetch_tiles claims ahead goes to L2 now, for
+                    // whichever block claims it (no claim is made)
+                    const int64_t pt = tile + p.prefetch_tiles;
+                    if (p.prefetch_tiles > 0 && pt < num_tiles) {
+                        const int64_t pph = phys_of(pt);
+                        const uint32_t pb =
+                            (static_cast<uint32_t>(count_of(pph)) * static_cast<uint32_t>(sizeof(T))) & ~15u;
+                        if (pb) bulk_prefetch_l2(in + pph * TILE, pb);
+                    }
                 }
             } else {
                 // ragged or misaligned: the aligned body by one bulk copy where
