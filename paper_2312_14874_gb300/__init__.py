@@ -18,6 +18,17 @@ Public API:
     rows(x, exclusive=...), backward(g, exclusive=...)    along the last dim, float32/float64
     cumsum(x, dim=-1, exclusive=False)                    differentiable (autograd)
     device_status(), copy_(dst, src), Workspace
+    resident_max_n(dtype)                                the largest input algo="resident" takes
+
+Algorithms (``algo=``): "auto" (the tuned table for this GPU, else the
+library's rule: the resident scan where it fits, the single-pass scan above),
+"single_pass" (chained scan with decoupled look-back), "two_pass" (reduce,
+scan of the tile sums, scan with offsets), "partitioned" (Section 2.2's cache
+partitioning with L2 as the cache) and "resident" (small inputs: one block
+per tile, every tile held in shared memory).  ``variant`` picks the launch
+shape (None: the tuned one).  The single-pass, partitioned and compaction
+kernels prefetch their input into L2 about 12 MiB ahead of their copies
+(environment variable GBSCAN_PREFETCH_BYTES; 1 turns it off).
 """
 from __future__ import annotations
 
