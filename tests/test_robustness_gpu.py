@@ -119,6 +119,60 @@ def test_race_stress_partitioned_small_chunks(tmp_path, lag):
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
 
 
+PREFETCH_CHECK = r"""
+import sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import oracle, synth
+import paper_2312_14874_gb300 as gb
+from paper_2312_14874_gb300 import _capi
+dev = torch.device("cuda", 0)
+n = 600 * 7168 + 1234   # several waves of tiles and a ragged tail
+a = synth.uniform_i32(n, 1 << 16, seed=21)
+x = torch.from_numpy(a).to(dev)
+ws = gb.Workspace(gb.workspace_bytes(torch.int64, _capi.KIND_SCAN, n))
+want = oracle.scan_i32(a)
+for algo in ("single_pass", "partitioned"):
+    for v in range(gb.num_variants(torch.int32)):
+        y = gb.inclusive(x, workspace=ws, algo=algo, variant=v).cpu().numpy()
+        assert np.array_equal(y, want), (algo, v)
+b = synth.uniform_i64(n, 1 << 32, seed=22)
+y = gb.inclusive(torch.from_numpy(b).to(dev), workspace=ws, algo="single_pass").cpu().numpy()
+assert np.array_equal(y, oracle.scan_i64(b))
+f = (synth.uniform_i32(n, 2, seed=23)).astype(np.uint8)
+for v in range(gb.num_variants(torch.int32, _capi.KIND_COMPACT)):
+    out, cnt = gb.compact(x, torch.from_numpy(f).to(dev), workspace=ws, variant=v)
+    k = int(cnt.item())
+    assert np.array_equal(out[:k].cpu().numpy(), oracle.compact(a, f)), v
+off = synth.segment_offsets(300, max_log2=14, seed=24)
+s_ = synth.uniform_i32(int(off[-1]), 4, seed=25)
+for v in range(gb.num_variants(torch.int32, _capi.KIND_SEGMENTED)):
+    ys = gb.segmented(torch.from_numpy(s_).to(dev), torch.from_numpy(off).to(dev), exclusive=True,
+                      variant=v).cpu().numpy()
+    assert np.array_equal(ys, oracle.seg_scan_i32(s_, off, True)), v
+assert gb.device_status(ws) == 0
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("pf_bytes", ["1", "65536", "1073741824"])
+def test_prefetch_distance_changes_no_result(tmp_path, pf_bytes):
+    """The L2 prefetch ahead of the claims is a hint: with it off (1), at one
+    tile ahead or less (64 KiB), and past the end of every input (1 GiB), the
+    single-pass, partitioned, compaction and segmented kernels give the
+    oracle's results (set in a child process: the distance is read once)."""
+    import os
+    import subprocess
+    import sys
+    from conftest import ROOT
+    script = tmp_path / "prefetch.py"
+    script.write_text(PREFETCH_CHECK)
+    env = dict(os.environ, GBSCAN_PREFETCH_BYTES=pf_bytes)
+    r = subprocess.run([sys.executable, str(script), ROOT], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
 # With a 2 ms spin limit, a launch that runs into a bounded wait must end
 # within its normal time plus the bounds it can meet in sequence: the first
 # wait to run out (a look-back or status wait: one spin limit; a pipeline wait:
