@@ -6,7 +6,10 @@
 //                 free) and starts a 1-D TMA bulk copy of it into that stage
 //                 (a ragged or misaligned tile: its aligned body by one bulk
 //                 copy, the rest by the lanes, padded with the operator's
-//                 neutral element);                                         [a1]
+//                 neutral element); with each claim it also asks L2 for the
+//                 tile about 12 MiB further on, claiming nothing, so that the
+//                 copy of that tile, whichever block claims it, comes from L2
+//                 instead of DRAM;                                          [a1]
 //   stage agents  one warp per stage: as soon as the stage's data lands it
 //                 sums the tile from shared memory, publishes the aggregate,
 //                 runs the two-level decoupled look-back (tiles of its 16-tile
@@ -32,9 +35,9 @@
 // prefix is known, so while a tile waits for its prefix it occupies registers
 // only; the stores hold no on-chip buffer.  On this part the rate of a chained
 // scan is set by the bytes each SM keeps between a tile's claim and its
-// prefix (about ten microseconds at full load: copy latency, aggregate,
-// look-back round trips), so the stages plus one tile of registers per block
-// are what the launch shapes trade.
+// prefix (copy latency, aggregate, look-back round trips), so the stages plus
+// one tile of registers per block are what the launch shapes trade, and the
+// L2 prefetch ahead of the claims takes the DRAM latency out of that time.
 //
 // Waits are bounded.  The consumers' stage wait and the sentinel that ends the
 // work are OR-reduced across the consumer warps in the named barrier that also
