@@ -192,6 +192,17 @@ __global__ void __launch_bounds__(THREADS, MINB) resident_scan_kernel(const Para
         bool ok;
         const Acc s = resident_prefix<Op>(p.rec, hdr, tile, epoch, cfg, lane, ok);
         if (lane == 0) c.prefix = s;
+        // The last tile's block, once its wait has ended, makes this launch's
+        // epoch the completed one (the next launch takes the one after).
+        // Every block reads the epoch in its first instructions, and the
+        // thread that read it later tags its tile's sum with it, so the sums
+        // this block has waited for show that their blocks have read it; all
+        // blocks are resident from the start of the launch, so a wait that
+        // ran out (200 ms by default) leaves no block unstarted.  Only the
+        // epoch wrap, which must clear every status word after the last block
+        // is done with them, goes through the done count (finish_launch).
+        if (lane == 0 && tile == static_cast<int64_t>(gridDim.x) - 1 && epoch != kEpochMask)
+            hdr->epoch = epoch;
     }
     __syncthreads();
 
@@ -218,10 +229,12 @@ __global__ void __launch_bounds__(THREADS, MINB) resident_scan_kernel(const Para
         if (whole) drain_fills<1>(&c.full, 1u, role_limit, hdr);
         bulk_wait_read_all();  // the store has read the block's shared memory before it is given up
     }
-    __syncthreads();
-    if (tid == 0) c.clear = finish_launch(hdr, epoch) ? 1u : 0u;
-    __syncthreads();
-    if (c.clear) clear_status_words(p.rec, p.rec_capacity, tid, blockDim.x);
+    if (epoch == kEpochMask) {  // the same for every block of the launch
+        __syncthreads();
+        if (tid == 0) c.clear = finish_launch(hdr, epoch) ? 1u : 0u;
+        __syncthreads();
+        if (c.clear) clear_status_words(p.rec, p.rec_capacity, tid, blockDim.x);
+    }
 }
 
 }  // namespace gbscan

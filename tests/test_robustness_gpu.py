@@ -119,6 +119,38 @@ def test_race_stress_partitioned_small_chunks(tmp_path, lag):
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
 
 
+EPOCH_MASK = (1 << 29) - 1  # status words carry a 29-bit launch epoch
+
+
+def test_epoch_wrap_every_algorithm():
+    """Launches across the epoch wrap (the workspace header's epoch set just
+    below 2^29 - 1): the wrapping launch clears every status word and the
+    launches after it start from epoch 1.  Every algorithm (the resident scan,
+    whose last block makes its epoch the completed one, included), int32 and
+    int64, and the segmented scan stay exact, with no device error."""
+    n = 40 * 7168 + 999
+    a = synth.uniform_i32(n, 1 << 16, seed=31)
+    b = synth.uniform_i64(n, 1 << 32, seed=32)
+    off = synth.segment_offsets(200, max_log2=12, seed=33)
+    sg = synth.uniform_i32(int(off[-1]), 4, seed=34)
+    x, xb = torch.from_numpy(a).to(dev()), torch.from_numpy(b).to(dev())
+    xs, o = torch.from_numpy(sg).to(dev()), torch.from_numpy(off).to(dev())
+    want, want64 = oracle.scan_i32(a), oracle.scan_i64(b)
+    wants = oracle.seg_scan_i32(sg, off, True)
+    ws = gb.Workspace(gb.workspace_bytes(torch.int64, _capi.KIND_SEGMENTED, n, off.size - 1))
+    for algo in ("resident", "single_pass", "two_pass", "partitioned"):
+        ws.buf[0:4].view(torch.int32).fill_(EPOCH_MASK - 2)  # the last completed epoch
+        for rep in range(5):  # epochs 2^29 - 2, 2^29 - 1 (the wrap), 1, 2, 3
+            y = gb.inclusive(x, workspace=ws, algo=algo).cpu().numpy()
+            assert np.array_equal(y, want), (algo, rep)
+            y = gb.inclusive(xb, workspace=ws, algo=algo).cpu().numpy()
+            assert np.array_equal(y, want64), (algo, rep)
+            y = gb.segmented(xs, o, exclusive=True, workspace=ws).cpu().numpy()
+            assert np.array_equal(y, wants), (algo, rep)
+        assert int(ws.buf[0:4].view(torch.int32).item()) < 64, algo  # wrapped
+        assert gb.device_status(ws) == 0, algo
+
+
 PREFETCH_CHECK = r"""
 import sys
 import numpy as np, torch
