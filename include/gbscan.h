@@ -73,8 +73,9 @@ typedef enum {
     GBSCAN_ALGO_PARTITIONED = 3,  /* cache-friendly partitioned two-pass (Section 2.2):
                                      per L2-sized chunk, reduce then scan from L2, one launch */
     GBSCAN_ALGO_RESIDENT = 4      /* small inputs, one launch: every tile held in shared
-                                     memory across a grid barrier between the reduce and
-                                     the scan (Figure 1b with Section 2.2's partitioning) */
+                                     memory from its reduce until the sums of the tiles
+                                     before it are written and its scan can finish
+                                     (Figure 1b with Section 2.2's partitioning) */
 } gbscan_algo;
 
 typedef enum {
@@ -126,11 +127,11 @@ gbscan_status gbscan_workspace_init(void* ws, size_t ws_bytes, cudaStream_t stre
  *               GBSCAN_CHUNK_LAG), RESIDENT (one cooperative launch, one block per tile
  *               of 5120 4-byte or 2560 8-byte elements, every block resident at once:
  *               each block keeps its tile in shared memory, writes the tile's sum, and
- *               after a grid-wide barrier adds the sums of the tiles before it; for
+ *               adds the sums of the tiles before it once they are written; for
  *               inputs of at most SMs x blocks-per-SM tiles, gbscan_resident_max_n;
  *               larger inputs return GBSCAN_ERR_UNSUPPORTED), or AUTO (RESIDENT where it fits;
- *               above that SINGLE_PASS, except compensated fp32 and fp64: TWO_PASS; the
- *               fastest choices measured on GB300).  SINGLE_PASS and PARTITIONED (and
+ *               above that SINGLE_PASS, except fp64: TWO_PASS; the fastest choices
+ *               measured on GB300).  SINGLE_PASS and PARTITIONED (and
  *               stream compaction) prefetch the input into L2 about 12 MiB ahead of their
  *               tile copies (environment variable GBSCAN_PREFETCH_BYTES; 1 turns it off).
  *   variant   : launch shape (threads, items per thread, pipeline stages), 0 = default;

@@ -233,10 +233,10 @@ static long long env_cached(std::atomic<long long>& cache, const char* name, lon
 
 // GBSCAN_ALGO_AUTO: the resident scan wherever it fits; above that the
 // single-pass scan (measured on GB300 with the L2 prefetch ahead of each
-// claim: the fastest of the four for int32, fp32 and int64 from 2^24 to 2^30
-// elements).  Compensated fp32 and fp64, whose scans are bound by arithmetic
-// (TwoSum pairs; fp64 adds), take the two-pass scan above the resident size
-// (their entry points decide that before calling scan_flat).
+// claim: the fastest of the four for int32, fp32, compensated fp32 and int64
+// from 2^24 to 2^30 elements).  fp64, whose scans are bound by its adds on
+// this part, takes the two-pass scan above the resident size (its entry
+// points decide that before calling scan_flat).
 
 int64_t partition_chunk_tiles(const Variant& v, size_t esz) {
     static std::atomic<long long> bytes_cache{0};
@@ -263,8 +263,8 @@ bool resident_fits(const Family& fam, int64_t n) {
     return cap > 0 && (n + fam.resident_tile - 1) / fam.resident_tile <= cap;
 }
 
-// GBSCAN_ALGO_AUTO for the scans bound by arithmetic (compensated fp32, fp64):
-// the resident scan where it fits, the two-pass scan above.
+// GBSCAN_ALGO_AUTO for the scans bound by arithmetic (fp64): the resident
+// scan where it fits, the two-pass scan above.
 gbscan_algo auto_arith_bound(const Family& fam, int64_t n, gbscan_algo algo) {
     if (algo != GBSCAN_ALGO_AUTO) return algo;
     return resident_fits(fam, n) ? GBSCAN_ALGO_RESIDENT : GBSCAN_ALGO_TWO_PASS;
@@ -543,7 +543,6 @@ static gbscan_status scan_f32_impl(const float* in, float* out, int64_t n, gbsca
                                    int variant, cudaStream_t stream) {
     if (mode != GBSCAN_F32_PLAIN && mode != GBSCAN_F32_COMPENSATED) return GBSCAN_ERR_INVALID_ARG;
     const Family& fam = mode == GBSCAN_F32_COMPENSATED ? family_scan_f32c() : family_scan_f32();
-    if (mode == GBSCAN_F32_COMPENSATED) algo = auto_arith_bound(fam, n, algo);
     return scan_flat(fam, in, out, n, sizeof(float), excl, ws, ws_bytes, algo, variant, stream);
 }
 

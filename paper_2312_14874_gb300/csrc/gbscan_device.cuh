@@ -636,6 +636,10 @@ struct OpF32C {
     __device__ static void accumulate(Acc& r, T x) { r.x = __fadd_rn(r.x, x); }
     __device__ static T output(Acc c, Acc l) { return __fadd_rn(c.x, l.x); }
     __device__ static T output1(Acc v) { return __fadd_rn(v.x, v.y); }
+    // in-tile sums of at most a warp row of 16-byte vectors (32 x 4 elements)
+    // run in plain fp32 and join the pairs exactly (lift): a row result is at
+    // most seven roundings deep (two in a vector, five across the row)
+    __device__ static T row_add(T a, T b) { return __fadd_rn(a, b); }
     __device__ static Bits to_bits(Acc a) {
         return (static_cast<Bits>(__float_as_uint(a.y)) << 32) | __float_as_uint(a.x);
     }
@@ -684,6 +688,17 @@ __device__ __forceinline__ typename Op::Acc run_init(typename Op::Acc c) {
     else
         return Op::identity();
 }
+
+// Whether short in-tile sums (a warp row of vectors, a group of a lane's
+// vectors) run in the element type (Op::row_add) and are lifted to the
+// accumulator afterwards: compensated pairs, for which such sums are short
+// enough for plain fp32.
+template <class Op, class = void>
+struct HasPlainRow : std::false_type {};
+template <class Op>
+struct HasPlainRow<Op, std::void_t<decltype(Op::row_add(std::declval<typename Op::T>(),
+                                                         std::declval<typename Op::T>()))>>
+    : std::true_type {};
 
 template <class Op>
 __device__ __forceinline__ typename Op::Acc shfl_up_acc(typename Op::Acc v, int d) {

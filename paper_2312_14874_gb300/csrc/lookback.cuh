@@ -116,8 +116,9 @@ __device__ __forceinline__ bool warp_spin_wait(uint64_t* bar, uint32_t parity, u
 // Sum of a whole stage by one warp: consecutive lanes on consecutive 16-byte
 // vectors, SU vectors in flight per lane with independent partial sums; each
 // vector is summed on its own (a run of VEC elements) and joined to its
-// partial sum with `combine`, so compensated pairs see runs of at most four
-// plain additions.
+// partial sum with `combine`.  Compensated pairs instead sum groups of four
+// of a lane's vectors as a tree in plain fp32 (four roundings deep) and join
+// each group's sum to one of two partial pairs.
 template <class Op, int TILE, int SU>
 __device__ __forceinline__ typename Op::Acc stage_sum(const unsigned char* stage, int lane) {
     using T = typename Op::T;
@@ -127,6 +128,37 @@ __device__ __forceinline__ typename Op::Acc stage_sum(const unsigned char* stage
     constexpr int U = PER_LANE < SU ? PER_LANE : SU;
     static_assert((TILE / VEC) % 32 == 0, "whole rows of vectors");
     const uint4* v4 = reinterpret_cast<const uint4*>(stage) + lane;
+    if constexpr (HasPlainRow<Op>::value) {
+        static_assert(VEC == 4 && PER_LANE % 4 == 0, "groups of four 4-element vectors");
+        constexpr int NG = PER_LANE / 4;
+        Acc part[2] = {Op::identity(), Op::identity()};
+#pragma unroll
+        for (int g0 = 0; g0 < NG; g0 += 2) {
+            uint4 w[2][4];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (g0 + u < NG) w[u][k] = v4[((g0 + u) * 4 + k) * 32];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (g0 + u < NG) {
+                    T sv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const T* e = reinterpret_cast<const T*>(&w[u][k]);
+                        sv[k] = Op::row_add(Op::row_add(e[0], e[1]), Op::row_add(e[2], e[3]));
+                    }
+                    const T t = Op::row_add(Op::row_add(sv[0], sv[1]), Op::row_add(sv[2], sv[3]));
+                    part[u] = combine_local<Op>(part[u], Op::lift(t));
+                }
+            }
+        }
+        Acc v = combine_local<Op>(part[0], part[1]);
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) v = combine_local<Op>(v, shfl_down_acc<Op>(v, d));
+        return shfl_idx_acc<Op>(v, 0);
+    }
     Acc part[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) part[u] = Op::identity();
@@ -323,18 +355,32 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_scan_kernel(c
             Acc rt[NV];  // row totals
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
-                Acc v = Op::lift(x[j][0]);
+                if constexpr (HasPlainRow<Op>::value) {
+                    // the row in the element type, its results lifted
+                    static_assert(VEC == 4, "4-element vectors");
+                    T inc = Op::row_add(Op::row_add(x[j][0], x[j][1]), Op::row_add(x[j][2], x[j][3]));
 #pragma unroll
-                for (int i = 1; i < VEC; ++i) Op::accumulate(v, x[j][i]);
-                Acc inc = v;
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const T o = __shfl_up_sync(0xffffffffu, inc, d);
+                        if (lane >= d) inc = Op::row_add(o, inc);
+                    }
+                    const T e = __shfl_up_sync(0xffffffffu, inc, 1);
+                    ex[j] = lane == 0 ? Op::identity() : Op::lift(e);
+                    rt[j] = Op::lift(__shfl_sync(0xffffffffu, inc, 31));
+                } else {
+                    Acc v = Op::lift(x[j][0]);
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const Acc o = shfl_up_acc<Op>(inc, d);
-                    if (lane >= d) inc = combine_local<Op>(o, inc);
+                    for (int i = 1; i < VEC; ++i) Op::accumulate(v, x[j][i]);
+                    Acc inc = v;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const Acc o = shfl_up_acc<Op>(inc, d);
+                        if (lane >= d) inc = combine_local<Op>(o, inc);
+                    }
+                    ex[j] = shfl_up_acc<Op>(inc, 1);
+                    if (lane == 0) ex[j] = Op::identity();
+                    rt[j] = shfl_idx_acc<Op>(inc, 31);
                 }
-                ex[j] = shfl_up_acc<Op>(inc, 1);
-                if (lane == 0) ex[j] = Op::identity();
-                rt[j] = shfl_idx_acc<Op>(inc, 31);
             }
             Acc wtot = rt[0];
 #pragma unroll

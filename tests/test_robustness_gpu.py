@@ -244,8 +244,8 @@ def test_dropped_tile_times_out_and_recovers(dtype, algo):
 
 
 def test_two_pass_compensated_stage_never_fills():
-    """The compensated fp32 scan (two-pass under AUTO) with one stage load never
-    issued, at 2^22 elements (hundreds of tiles per block): the block whose
+    """The compensated fp32 two-pass scan (AUTO's pick at 2^22) with one stage
+    load never issued, at 2^22 elements (hundreds of tiles per block): the block whose
     stage never fills stops at once instead of paying the bound on every later
     tile; both passes end within the bound with TIMEOUT, and the next call on
     the same workspace is correct again."""
