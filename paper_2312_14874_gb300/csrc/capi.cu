@@ -425,10 +425,11 @@ gbscan_status compact_impl(const void* in, const uint8_t* flags, void* out, int6
     Params p = make_params(in, out, n, v.tile, ws, ws_bytes);
     p.flags = flags;
     p.total_out = reinterpret_cast<unsigned long long*>(count);
+    p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, 4);
+    if (v.single_pass) return from_cuda(v.single_pass(p, stream));  // the single-pass compaction
     // whole R groups per chunk
     p.chunk_tiles = (partition_chunk_tiles(v, 4) + kCpGroup - 1) / kCpGroup * kCpGroup;
     p.chunk_lag = partition_chunk_lag();
-    p.prefetch_tiles = single_pass_prefetch_tiles(v.tile, 4);
     return from_cuda(v.partitioned(p, stream));
 }
 

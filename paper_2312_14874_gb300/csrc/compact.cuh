@@ -2,8 +2,10 @@
 // whose keep flag is nonzero, in order, and the number kept.
 //
 // The exclusive scan of the 0/1 keep flags (Section 1's definition over the
-// flags) gives every kept element its position in the output.  The scan is the
-// partitioned one (Section 2.2): a work list of reduce items R and scan items
+// flags) gives every kept element its position in the output.  Two kernels:
+// compact_kernel runs the partitioned scan (Section 2.2), and lb_compact_kernel
+// (at the end of this file) the single-pass chained scan, the faster below
+// about 2^26 elements.  compact_kernel: a work list of reduce items R and scan items
 // S, S(c) interleaved with R(c + lag); the chunk scanner warp turns a chunk's
 // tile counts into tile offsets and chains the chunk prefixes.  An R item
 // counts the kept elements of kCpGroup consecutive tiles from their flags alone
@@ -23,6 +25,7 @@
 // 14336 elements.
 #pragma once
 
+#include "lookback.cuh"
 #include "partitioned.cuh"
 
 namespace gbscan {
@@ -509,6 +512,301 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
         bulk_wait_all();
         c.clear = finish_launch(hdr, epoch) ? 1u : 0u;
     }
+    __syncthreads();
+    if (c.clear) clear_status_words(p.rec, p.rec_capacity, tid, blockDim.x);
+}
+
+// ---- the compaction on the single-pass chained scan ------------------------
+//
+// lb_compact_kernel: the roles of the single-pass look-back kernel
+// (lookback.cuh) applied to the keep flags, one pass over the data.
+//   loader     claims a tile when a stage is free and copies the tile's
+//              payload and its flags into the stage (bulk copies; a ragged or
+//              misaligned tile partly by the lanes, its flags padded with 0);
+//              it asks L2 for the payload and flags about 12 MiB ahead;
+//   agents     one warp per stage: counts the tile's kept elements from the
+//              staged flags, publishes the count and looks back over the
+//              earlier tiles' counts (the exclusive scan of the counts, Section
+//              1's definition over the flags); the tile's exclusive count is
+//              its first output position.  The last tile's agent writes the
+//              total;
+//   consumers  NW warps read the stage at once (lane l of warp w: the 16-byte
+//              payload vectors w*NV*32 + j*32 + l and their four flags) and
+//              give it back; three ballots of the lane counts per row of 32
+//              vectors give every lane its kept elements' places in the row,
+//              and the warps exchange their kept counts.  Once the tile's
+//              position is known, each warp places a row's kept elements in
+//              order in a small row buffer of its own in shared memory and
+//              writes them with coalesced stores, row after row.
+// A tile waits for its position in registers, not in a stage, so the stages
+// are refilled as soon as they are read and the shared memory holds stages
+// only (the bytes in flight per SM set the rate of a chained scan here).
+template <int NW, int STAGES>
+struct LbcCtrl {
+    uint64_t full[STAGES];   // stage data landed
+    uint64_t empty[STAGES];  // count 2: the consumers have read the stage, its agent is idle
+    uint64_t ready[STAGES];  // the agent has put the tile's position in excl
+    int64_t tile_id[STAGES];
+    unsigned long long excl[STAGES][2];  // by use parity, as in the look-back scan
+    uint32_t wtot[NW];
+    uint32_t epoch;
+    uint32_t clear;
+};
+
+template <int NW, int NV>
+__host__ __device__ constexpr int lbc_tile() {
+    return NW * 32 * NV * 4;
+}
+
+// Two 128-element row buffers per consumer warp (a row of 32 vectors).
+constexpr int kLbcRowBuf = 2 * 128;
+
+// Stages (payload, then flags), the warps' row buffers, the control block.
+template <int NW, int NV, int STAGES>
+constexpr int lbc_smem_bytes() {
+    return STAGES * lbc_tile<NW, NV>() * 5 + NW * kLbcRowBuf * 4 +
+           static_cast<int>(sizeof(LbcCtrl<NW, STAGES>));
+}
+
+template <int NW, int STAGES>
+constexpr int lbc_threads() {
+    return (NW + 1 + STAGES) * 32;
+}
+
+// The number of nonzero bytes of a word (each byte's bits ORed into its bit 0).
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t t) {
+    t |= t >> 4;
+    t |= t >> 2;
+    t |= t >> 1;
+    return __popc(t & 0x01010101u);
+}
+
+template <int NW, int NV, int STAGES, int LB, int MINB>
+__global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_compact_kernel(const Params p) {
+    using Op = OpI64;  // the counts
+    using T = uint32_t;
+    constexpr int NT = NW * 32;
+    constexpr int TILE = lbc_tile<NW, NV>();
+    constexpr int TILE_BYTES = TILE * 4;
+    constexpr int STAGE_BYTES = TILE_BYTES + TILE;  // payload, then flags
+    constexpr int LOAD_WARP = NW;                   // warps NW+1+s: the agent of stage s
+    static_assert(STAGES >= 2, "at least two stages");
+    static_assert((TILE / 16) % 32 == 0, "whole rows of flag vectors for the agents");
+    using CtrlT = LbcCtrl<NW, STAGES>;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* rowbufs = reinterpret_cast<T*>(smem + STAGES * STAGE_BYTES);
+    CtrlT& c = *reinterpret_cast<CtrlT*>(smem + STAGES * STAGE_BYTES + NW * kLbcRowBuf * 4);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    Header* hdr = p.hdr;
+    const int64_t num_tiles = p.num_tiles;
+
+    unsigned int first_claim = 0;
+    if (warp == LOAD_WARP && lane == 0) first_claim = atomicAdd(&hdr->tile_counter, 1u);
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&c.full[s], 1);
+            mbar_init(&c.empty[s], 2);
+            mbar_init(&c.ready[s], 1);
+        }
+        fence_mbar_init();
+        c.epoch = hdr->epoch;
+        c.clear = 0;
+    }
+    __syncthreads();
+    const uint32_t epoch = launch_epoch(c.epoch);
+    const LookbackCfg cfg = read_lookback_cfg(hdr);
+    const uint64_t role_limit = 4 * cfg.spin_limit_ns + 10000000ull;
+    auto count_of = [&](int64_t t) -> int {
+        const int64_t rem = p.n - t * TILE;
+        return rem < TILE ? static_cast<int>(rem) : TILE;
+    };
+    auto payload = [&](int s) { return reinterpret_cast<T*>(smem + s * STAGE_BYTES); };
+    auto flagbuf = [&](int s) { return smem + s * STAGE_BYTES + TILE_BYTES; };
+
+    if (warp == LOAD_WARP) {
+        const T* __restrict__ in = static_cast<const T*>(p.in);
+        const uint8_t* __restrict__ fl = p.flags;
+        const bool in_al = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+        const bool fl_al = (reinterpret_cast<uintptr_t>(fl) & 15) == 0;
+        const uint64_t evict_first = l2_policy_evict_first();
+        uint32_t fills = 0;
+        for (uint32_t k = 0;; ++k) {
+            const int s = static_cast<int>(k % STAGES);
+            const uint32_t use = k / STAGES;
+            if (use > 0 && !warp_wait(&c.empty[s], (use - 1) & 1u, role_limit, hdr, epoch, lane))
+                break;
+            long long claimed = 0;
+            if (lane == 0)
+                claimed = static_cast<long long>(k == 0 ? first_claim : atomicAdd(&hdr->tile_counter, 1u));
+            const int64_t tile = __shfl_sync(0xffffffffu, claimed, 0);
+            if (tile >= num_tiles) {
+                // an end sentinel in this stage and the next STAGES-1
+                if (lane == 0) {
+                    c.tile_id[s] = tile;
+                    mbar_arrive(&c.full[s]);
+                }
+                ++fills;
+                for (uint32_t k2 = k + 1; k2 < k + STAGES; ++k2) {
+                    const int s2 = static_cast<int>(k2 % STAGES);
+                    const uint32_t use2 = k2 / STAGES;
+                    if (use2 > 0 &&
+                        !warp_wait(&c.empty[s2], (use2 - 1) & 1u, role_limit, hdr, epoch, lane))
+                        break;
+                    if (lane == 0) {
+                        c.tile_id[s2] = num_tiles;
+                        mbar_arrive(&c.full[s2]);
+                    }
+                    ++fills;
+                }
+                break;
+            }
+            const int cnt = count_of(tile);
+            T* xb = payload(s);
+            uint8_t* fb = flagbuf(s);
+            if (in_al && fl_al && cnt == TILE) {
+                if (lane == 0) {
+                    c.tile_id[s] = tile;
+                    mbar_arrive_expect_tx(&c.full[s], TILE_BYTES + TILE);
+                    bulk_load_hint(xb, in + tile * TILE, TILE_BYTES, &c.full[s], evict_first);
+                    bulk_load_hint(fb, fl + tile * TILE, TILE, &c.full[s], evict_first);
+                    // the tile prefetch_tiles ahead, into L2 for whichever block
+                    // claims it (no claim is made)
+                    const int64_t pt = tile + p.prefetch_tiles;
+                    if (p.prefetch_tiles > 0 && pt < num_tiles) {
+                        const uint32_t pc = static_cast<uint32_t>(count_of(pt));
+                        if ((pc * 4u) & ~15u) bulk_prefetch_l2(in + pt * TILE, (pc * 4u) & ~15u);
+                        if (pc & ~15u) bulk_prefetch_l2(fl + pt * TILE, pc & ~15u);
+                    }
+                }
+            } else {
+                // ragged or misaligned: aligned bodies by bulk copies, the rest
+                // by the lanes; the flags padded with 0 to the whole tile
+                const uint32_t xbytes = warp_stage_partial<T>(xb, in + tile * TILE, cnt, cnt, in_al, T(0), lane);
+                const uint32_t fbytes =
+                    warp_stage_partial<uint8_t>(fb, fl + tile * TILE, cnt, TILE, fl_al, uint8_t(0), lane);
+                __syncwarp();
+                if (lane == 0) {
+                    c.tile_id[s] = tile;
+                    if (xbytes + fbytes) {
+                        mbar_arrive_expect_tx(&c.full[s], xbytes + fbytes);
+                        if (xbytes) bulk_load(xb, in + tile * TILE, xbytes, &c.full[s]);
+                        if (fbytes) bulk_load(fb, fl + tile * TILE, fbytes, &c.full[s]);
+                    } else {
+                        mbar_arrive(&c.full[s]);
+                    }
+                }
+            }
+            ++fills;
+        }
+        if (lane == 0) drain_fills<STAGES>(c.full, fills, role_limit, hdr);
+    } else if (warp > LOAD_WARP) {
+        // ---- the stage's agent: the tile's count, look-back, position -------
+        const int s = warp - LOAD_WARP - 1;
+        for (uint32_t use = 0;; ++use) {
+            if (!warp_spin_wait(&c.full[s], use & 1u, role_limit, hdr, epoch, lane)) break;
+            const int64_t tile = *static_cast<volatile int64_t*>(&c.tile_id[s]);
+            if (tile >= num_tiles) break;
+            const uint4* f4 = reinterpret_cast<const uint4*>(flagbuf(s)) + lane;
+            uint32_t kept = 0;
+#pragma unroll
+            for (int q = 0; q < TILE / 16 / 32; ++q) {
+                const uint4 w = f4[q * 32];
+                kept += nonzero_bytes(w.x) + nonzero_bytes(w.y) + nonzero_bytes(w.z) + nonzero_bytes(w.w);
+            }
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, d);
+            const unsigned long long agg = kept;
+            __syncwarp();
+            if (lane == 0) publish_aggregate<Op>(p.rec, tile, epoch, cfg, false, agg);
+            bool ef;
+            unsigned long long ev;
+            lookback<Op, kNoHeads, LB>(p.rec, hdr, tile, epoch, cfg, false, agg, lane, ef, ev);
+            if (lane == 0) {
+                c.excl[s][use & 1u] = ev;
+                if (tile == num_tiles - 1 && p.total_out) *p.total_out = ev + agg;
+                mbar_arrive(&c.ready[s]);
+                mbar_arrive(&c.empty[s]);  // idle again: the stage may be refilled
+            }
+        }
+    } else {
+        // ---- consumers: places, the warps' runs, stores -----------------------
+        T* out = static_cast<T*>(p.out);
+        T* rb = rowbufs + warp * kLbcRowBuf;
+        const int vbase = warp * NV * 32 + lane;  // this lane's first vector in the tile
+        const uint32_t below = (1u << lane) - 1u;
+        for (uint32_t k = 0;; ++k) {
+            const int s = static_cast<int>(k % STAGES);
+            const uint32_t use = k / STAGES;
+            const bool ok = warp_spin_wait(&c.full[s], use & 1u, role_limit, hdr, epoch, lane);
+            const int64_t tile = *static_cast<volatile int64_t*>(&c.tile_id[s]);
+            bool stop = !ok || tile >= num_tiles;
+            const uint4* x4 = reinterpret_cast<const uint4*>(payload(s));
+            const uint32_t* f1 = reinterpret_cast<const uint32_t*>(flagbuf(s));
+            uint4 x[NV];
+            uint32_t m[NV];   // the vector's four keep bits (bit i: element 4v+i)
+            uint32_t ex[NV];  // the row's kept elements before this lane's
+            uint32_t rt[NV];  // the row's kept elements
+            uint32_t wk = 0;  // the warp's kept elements (the same in every lane)
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                const int v = vbase + j * 32;
+                x[j] = x4[v];
+                // the bytes' ORed-down bits, gathered by one multiply
+                uint32_t t = f1[v];
+                t |= t >> 4;
+                t |= t >> 2;
+                t |= t >> 1;
+                t &= 0x01010101u;
+                m[j] = (t * 0x01020408u) >> 24;
+                const uint32_t n = __popc(m[j]);
+                const uint32_t b0 = __ballot_sync(0xffffffffu, n & 1u);
+                const uint32_t b1 = __ballot_sync(0xffffffffu, n & 2u);
+                const uint32_t b2 = __ballot_sync(0xffffffffu, n & 4u);
+                ex[j] = __popc(b0 & below) + 2u * __popc(b1 & below) + 4u * __popc(b2 & below);
+                rt[j] = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
+                wk += rt[j];
+            }
+            if (lane == 0) c.wtot[warp] = wk;
+            // kept counts exchanged; every consumer warp agrees on going on
+            stop = named_barrier_or<NT>(1, stop);
+            if (stop) break;
+            if (tid == 0) mbar_arrive(&c.empty[s]);  // every consumer has read the stage
+            uint32_t woff = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+                if (w < warp) woff += c.wtot[w];
+            const bool rok = warp_spin_wait(&c.ready[s], use & 1u, role_limit, hdr, epoch, lane);
+            const unsigned long long base = c.excl[s][use & 1u] + woff;
+            named_barrier_sync<NT>(1);  // counts read before the next tile writes them
+            // a run that would leave the output (only after a failed wait, which
+            // has recorded its error) is not written
+            if (rok && base <= static_cast<unsigned long long>(p.n) &&
+                wk <= static_cast<unsigned long long>(p.n) - base) {
+                T* o = out + base;
+#pragma unroll
+                for (int j = 0; j < NV; ++j) {
+                    // the row's kept elements in order in row buffer j & 1 (its
+                    // last reads, two rows back, came before the last __syncwarp)
+                    T* b = rb + (j & 1) * 128;
+                    uint32_t q = ex[j];
+                    if (m[j] & 1u) b[q++] = x[j].x;
+                    if (m[j] & 2u) b[q++] = x[j].y;
+                    if (m[j] & 4u) b[q++] = x[j].z;
+                    if (m[j] & 8u) b[q] = x[j].w;
+                    __syncwarp();
+                    for (uint32_t i = lane; i < rt[j]; i += 32) o[i] = b[i];
+                    o += rt[j];
+                }
+            }
+            __syncwarp();  // the row buffers are read before the next tile's placements
+        }
+    }
+
+    __syncthreads();
+    if (tid == 0) c.clear = finish_launch(hdr, epoch) ? 1u : 0u;
     __syncthreads();
     if (c.clear) clear_status_words(p.rec, p.rec_capacity, tid, blockDim.x);
 }

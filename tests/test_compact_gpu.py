@@ -43,27 +43,31 @@ def test_compact_sizes_and_densities(key, density):
 
 
 def test_compact_misaligned_and_bool_flags():
+    """Every variant (the partitioned and the single-pass compaction) on a
+    payload and flags at odd offsets (element-wise loads), bool flags, and an
+    output at an odd offset between guard words."""
     n = 4 * 5120 + 77
     a = synth.uniform_i32(n + 1, 1 << 30, seed=4)
     f = flags_of(n + 1, 0.3, seed=5)
     xa = torch.from_numpy(a).to(dev())
     fa = torch.from_numpy(f).to(dev())
-    # payload at an element offset (not 16-byte aligned), flags at a byte offset
-    x, fl = xa[1:], fa[1:]
-    out, cnt = gb.compact(x, fl)
-    want = oracle.compact(a[1:], f[1:])
-    assert int(cnt.item()) == want.size
-    assert np.array_equal(out[:want.size].cpu().numpy(), want)
-    out, cnt = gb.compact(xa[:n], fa[:n] != 0)  # bool flags
-    want = oracle.compact(a[:n], f[:n])
-    assert int(cnt.item()) == want.size and np.array_equal(out[:want.size].cpu().numpy(), want)
-    # output at an element offset (not 16-byte aligned): the runs leave with
-    # single-element stores; the guard words around it stay untouched
-    ob = torch.full((n + 2,), -7, dtype=torch.int32, device=dev())
-    out, cnt = gb.compact(xa[:n], fa[:n], out=ob[1:n + 1])
-    k = int(cnt.item())
-    assert k == want.size and np.array_equal(out[:k].cpu().numpy(), want)
-    assert int(ob[0].item()) == -7 and int(ob[n + 1].item()) == -7
+    for v in range(gb.num_variants(torch.int32, _capi.KIND_COMPACT)):
+        # payload at an element offset (not 16-byte aligned), flags at a byte offset
+        x, fl = xa[1:], fa[1:]
+        out, cnt = gb.compact(x, fl, variant=v)
+        want = oracle.compact(a[1:], f[1:])
+        assert int(cnt.item()) == want.size, v
+        assert np.array_equal(out[:want.size].cpu().numpy(), want), v
+        out, cnt = gb.compact(xa[:n], fa[:n] != 0, variant=v)  # bool flags
+        want = oracle.compact(a[:n], f[:n])
+        assert int(cnt.item()) == want.size and np.array_equal(out[:want.size].cpu().numpy(), want), v
+        # output at an element offset (not 16-byte aligned): the runs leave with
+        # single-element stores; the guard words around it stay untouched
+        ob = torch.full((n + 2,), -7, dtype=torch.int32, device=dev())
+        out, cnt = gb.compact(xa[:n], fa[:n], out=ob[1:n + 1], variant=v)
+        k = int(cnt.item())
+        assert k == want.size and np.array_equal(out[:k].cpu().numpy(), want), v
+        assert int(ob[0].item()) == -7 and int(ob[n + 1].item()) == -7, v
     assert gb.device_status() == 0
 
 

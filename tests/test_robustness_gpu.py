@@ -243,6 +243,33 @@ def test_dropped_tile_times_out_and_recovers(dtype, algo):
     assert gb.device_status(ws) == 0
 
 
+def test_compact_dropped_tile_times_out_and_recovers():
+    """Stream compaction, every variant (the partitioned one and the one on the
+    single-pass look-back): a tile whose kept count is never published makes
+    the waits on it run out; the launch ends within the bound with TIMEOUT and
+    writes nothing outside the output, and the workspace works again once the
+    hook is removed."""
+    import time
+    n = 50 * 5120
+    x = torch.arange(n, dtype=torch.int32, device=dev())
+    f = torch.ones(n, dtype=torch.uint8, device=dev())
+    ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_COMPACT, n))
+    for v in range(gb.num_variants(torch.int32, _capi.KIND_COMPACT)):
+        ob = torch.full((n + 2,), -7, dtype=torch.int32, device=dev())
+        gb.set_debug(spin_limit_us=2000, drop_tile=17, workspace=ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gb.compact(x, f, out=ob[1:n + 1], workspace=ws, variant=v)
+        torch.cuda.synchronize()
+        assert time.perf_counter() - t0 < LAUNCH_BOUND_S, v
+        assert gb.device_status(ws) == _capi.ERR_TIMEOUT, v
+        assert int(ob[0].item()) == -7 and int(ob[n + 1].item()) == -7, v
+        gb.set_debug(workspace=ws)
+        out, cnt = gb.compact(x, f, workspace=ws, variant=v)
+        assert int(cnt.item()) == n and torch.equal(out, x), v
+        assert gb.device_status(ws) == 0, v
+
+
 def test_two_pass_compensated_stage_never_fills():
     """The compensated fp32 two-pass scan (AUTO's pick at 2^22) with one stage
     load never issued, at 2^22 elements (hundreds of tiles per block): the block whose
