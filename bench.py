@@ -71,7 +71,7 @@ def parse_args(argv=None):
     prof.add_argument("--dtype", choices=["i32", "i64", "f32", "f32c"], default="i32",
                       help="scan case: element type (f32c = compensated fp32)")
     prof.add_argument("--n", type=int, default=None, help="scan case: element count (else 2^--n-log2)")
-    prof.add_argument("--variant", type=int, default=None, help="scan case: launch shape (else tuned)")
+    prof.add_argument("--variant", type=int, default=None, help="scan and compact_i32 cases: launch shape (else tuned)")
     prof.add_argument("--reps", type=int, default=4, help="launches of the case")
     return ap.parse_args(argv)
 
@@ -472,7 +472,8 @@ def profile_case(args) -> int:
                  when not given)
     seg_f32      the exclusive segmented scan of 20,000 segments with lengths
                  log-uniform in [1, 2^16] (116,893,251 fp32 elements, U[0,1))
-    compact_i32  stream compaction of 2^28 int32 elements with half kept
+    compact_i32  stream compaction of 2^28 int32 elements with half kept, with
+                 --variant (tuned when not given)
     """
     import torch
     import paper_2312_14874_gb300 as gb
@@ -516,9 +517,9 @@ def profile_case(args) -> int:
         ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_COMPACT, n), dev)
         count = None
         for _ in range(args.reps):
-            _, count = gb.compact(x, flags, out=y, workspace=ws)
+            _, count = gb.compact(x, flags, out=y, workspace=ws, variant=args.variant)
         torch.cuda.synchronize(dev)
-        print(f"compact_i32: n={n}, kept={int(count.item())}, launches={args.reps}, "
+        print(f"compact_i32: n={n}, variant={args.variant}, kept={int(count.item())}, launches={args.reps}, "
               f"status={gb.device_status(ws, dev)}")
     return 0
 

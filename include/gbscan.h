@@ -280,7 +280,7 @@ gbscan_status scan_segmented_op_f32(const float* in, float* out, int64_t n,
  *   out[j] = in[i_j] for the kept indices i_0 < i_1 < ..., j < *count,
  *   *count = the number of kept elements (a DEVICE int64, written on `stream`).
  * One launch: the scan of the flags fused with the gather (no flag prefix
- * reaches memory); variants 0-2 run the partitioned scan, 3-4 the single-pass
+ * reaches memory); variants 0-2 run the partitioned scan, 3 the single-pass
  * chained scan with decoupled look-back (the faster below about 2^26
  * elements; the tuned choice by size takes it there).  in/out: device arrays of n 4-byte elements
  * (copied bit for bit), not overlapping; flags: n device bytes; out must hold

@@ -535,12 +535,16 @@ __global__ void __launch_bounds__((CWARPS + 2) * 32, MINB) compact_kernel(const 
 //              give it back; three ballots of the lane counts per row of 32
 //              vectors give every lane its kept elements' places in the row,
 //              and the warps exchange their kept counts.  Once the tile's
-//              position is known, each warp places a row's kept elements in
-//              order in a small row buffer of its own in shared memory and
-//              writes them with coalesced stores, row after row.
+//              position is known, every lane stores its kept elements at
+//              their places straight from registers (consecutive lanes'
+//              elements are adjacent, so each store instruction covers a
+//              few hundred contiguous bytes).
 // A tile waits for its position in registers, not in a stage, so the stages
 // are refilled as soon as they are read and the shared memory holds stages
 // only (the bytes in flight per SM set the rate of a chained scan here).
+// Measured against placing each row in a shared-memory row buffer first and
+// storing it with one coalesced store per 32 elements: fewer instructions,
+// 4366 against 3868 GB/s at int32 2^30 with half kept.
 template <int NW, int STAGES>
 struct LbcCtrl {
     uint64_t full[STAGES];   // stage data landed
@@ -558,14 +562,10 @@ __host__ __device__ constexpr int lbc_tile() {
     return NW * 32 * NV * 4;
 }
 
-// Two 128-element row buffers per consumer warp (a row of 32 vectors).
-constexpr int kLbcRowBuf = 2 * 128;
-
-// Stages (payload, then flags), the warps' row buffers, the control block.
+// Stages (payload, then flags), then the control block.
 template <int NW, int NV, int STAGES>
 constexpr int lbc_smem_bytes() {
-    return STAGES * lbc_tile<NW, NV>() * 5 + NW * kLbcRowBuf * 4 +
-           static_cast<int>(sizeof(LbcCtrl<NW, STAGES>));
+    return STAGES * lbc_tile<NW, NV>() * 5 + static_cast<int>(sizeof(LbcCtrl<NW, STAGES>));
 }
 
 template <int NW, int STAGES>
@@ -595,8 +595,7 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_compact_kerne
     using CtrlT = LbcCtrl<NW, STAGES>;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    T* rowbufs = reinterpret_cast<T*>(smem + STAGES * STAGE_BYTES);
-    CtrlT& c = *reinterpret_cast<CtrlT*>(smem + STAGES * STAGE_BYTES + NW * kLbcRowBuf * 4);
+    CtrlT& c = *reinterpret_cast<CtrlT*>(smem + STAGES * STAGE_BYTES);
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -734,7 +733,6 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_compact_kerne
     } else {
         // ---- consumers: places, the warps' runs, stores -----------------------
         T* out = static_cast<T*>(p.out);
-        T* rb = rowbufs + warp * kLbcRowBuf;
         const int vbase = warp * NV * 32 + lane;  // this lane's first vector in the tile
         const uint32_t below = (1u << lane) - 1u;
         for (uint32_t k = 0;; ++k) {
@@ -786,22 +784,17 @@ __global__ void __launch_bounds__((NW + 1 + STAGES) * 32, MINB) lb_compact_kerne
             if (rok && base <= static_cast<unsigned long long>(p.n) &&
                 wk <= static_cast<unsigned long long>(p.n) - base) {
                 T* o = out + base;
+                // each lane stores its kept elements at their places
 #pragma unroll
                 for (int j = 0; j < NV; ++j) {
-                    // the row's kept elements in order in row buffer j & 1 (its
-                    // last reads, two rows back, came before the last __syncwarp)
-                    T* b = rb + (j & 1) * 128;
                     uint32_t q = ex[j];
-                    if (m[j] & 1u) b[q++] = x[j].x;
-                    if (m[j] & 2u) b[q++] = x[j].y;
-                    if (m[j] & 4u) b[q++] = x[j].z;
-                    if (m[j] & 8u) b[q] = x[j].w;
-                    __syncwarp();
-                    for (uint32_t i = lane; i < rt[j]; i += 32) o[i] = b[i];
+                    if (m[j] & 1u) o[q++] = x[j].x;
+                    if (m[j] & 2u) o[q++] = x[j].y;
+                    if (m[j] & 4u) o[q++] = x[j].z;
+                    if (m[j] & 8u) o[q] = x[j].w;
                     o += rt[j];
                 }
             }
-            __syncwarp();  // the row buffers are read before the next tile's placements
         }
     }
 

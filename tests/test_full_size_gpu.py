@@ -30,7 +30,7 @@ import torch
 import oracle
 import synth
 import paper_2312_14874_gb300 as gb
-from paper_2312_14874_gb300 import autotune
+from paper_2312_14874_gb300 import _capi, autotune
 from paper_2312_14874_gb300.graphs import SegmentedScanGraph
 
 pytestmark = pytest.mark.gpu
@@ -87,16 +87,22 @@ def test_int32_2e30_running_max_min(op):
 
 
 def test_compact_int32_2e30_half_kept():
+    """Every compaction variant (the partitioned one, which the tuned table
+    takes at this size, and the single-pass one)."""
     n = 1 << 30
     a = synth.uniform_i32(n, 1 << 31, seed=1)
     f = (synth.unit_f32(n, seed=2) < 0.5).astype(np.uint8)
     want = oracle.compact(a, f)
-    out, cnt = gb.compact(torch.from_numpy(a).to(dev()), torch.from_numpy(f).to(dev()))
-    k = int(cnt.item())
-    assert k == want.size
-    assert np.array_equal(out[:k].cpu().numpy(), want)
+    x, fl = torch.from_numpy(a).to(dev()), torch.from_numpy(f).to(dev())
+    out = torch.empty_like(x)
+    for v in range(gb.num_variants(torch.int32, _capi.KIND_COMPACT)):
+        out.fill_(-1)
+        _, cnt = gb.compact(x, fl, out=out, variant=v)
+        k = int(cnt.item())
+        assert k == want.size, v
+        assert np.array_equal(out[:k].cpu().numpy(), want), v
     assert gb.device_status() == 0
-    record("compact_i32_2^30_half_kept", f"bit-exact, kept {k}")
+    record("compact_i32_2^30_half_kept", f"bit-exact in every variant, kept {k}")
 
 
 def test_int64_2e29_every_algorithm():
