@@ -151,6 +151,26 @@ def test_epoch_wrap_every_algorithm():
         assert gb.device_status(ws) == 0, algo
 
 
+def test_epoch_wrap_compaction():
+    """Stream compaction across the epoch wrap, every variant (the partitioned
+    and the single-pass compaction): exact outputs and counts, the wrapping
+    launch clears the status words, no device error."""
+    n = 40 * 5120 + 999
+    a = synth.uniform_i32(n, 1 << 30, seed=35)
+    f = (synth.unit_f32(n, seed=36) < 0.4).astype(np.uint8)
+    want = oracle.compact(a, f)
+    x, fl = torch.from_numpy(a).to(dev()), torch.from_numpy(f).to(dev())
+    ws = gb.Workspace(gb.workspace_bytes(torch.int32, _capi.KIND_COMPACT, n))
+    for v in range(gb.num_variants(torch.int32, _capi.KIND_COMPACT)):
+        ws.buf[0:4].view(torch.int32).fill_(EPOCH_MASK - 2)  # the last completed epoch
+        for rep in range(5):  # epochs 2^29 - 2, 2^29 - 1 (the wrap), 1, 2, 3
+            out, cnt = gb.compact(x, fl, workspace=ws, variant=v)
+            k = int(cnt.item())
+            assert k == want.size and np.array_equal(out[:k].cpu().numpy(), want), (v, rep)
+        assert int(ws.buf[0:4].view(torch.int32).item()) < 64, v  # wrapped
+        assert gb.device_status(ws) == 0, v
+
+
 PREFETCH_CHECK = r"""
 import sys
 import numpy as np, torch
