@@ -10,7 +10,7 @@ with 8 * 2^30 bytes per step; inputs (4 GiB) and outputs are larger than the
 
 Prints one JSON line (rank 0).  Extra fields: the roofline of the timed
 kernel against the measured HBM copy bandwidth; the single-pass decoupled
-look-back kernel's own figure at the same size (north_star_single_pass); the
+look-back kernel's own figure at the same size (single_pass_vs_copy); the
 end-to-end number through the public API with host buffers, next to a
 copy-only run of the same host-link schedule; SM clocks sampled during the
 timed region; the CPU oracle timed on a bounded sample (cpu_baseline); and
@@ -611,7 +611,7 @@ def main(argv=None) -> int:
     torch.cuda.synchronize(dev)
     if int(y[-1].item()) % (1 << 32) != total:
         raise RuntimeError("single-pass result failed the last == total check")
-    north_star = {"kernel": "single-pass chained scan with decoupled look-back (lb_scan_kernel)",
+    sp_vs_copy = {"kernel": "single-pass chained scan with decoupled look-back (lb_scan_kernel)",
                   "variant": sp_variant, "ms": round(sp_ms, 4),
                   "gbs": round(BYTES_PER_STEP / (sp_ms * 1e-3) / 1e9, 1),
                   "copy_gbs_same_run": round(BYTES_PER_STEP / (cp_ms * 1e-3) / 1e9, 1),
@@ -734,7 +734,7 @@ def main(argv=None) -> int:
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"],
                        "power_w_max": clk.get("power_w_max")},
-            "north_star_single_pass": north_star,
+            "single_pass_vs_copy": sp_vs_copy,
             "cpu_baseline": cpu,
             "elements_per_s": round(value * 1e9 / 8, 1),
             "side": side,
