@@ -124,6 +124,26 @@ def test_variant_table():
     assert L.gbscan_num_variants(_capi.I64, _capi.KIND_SEGMENTED) == 0
 
 
+def test_compaction_variant_table():
+    """Compaction variants 0-2 are the partitioned kernel (consumer warps plus a
+    loader and a scanner warp), variant 3 the single-pass one (consumer warps
+    plus a loader and one agent warp per stage); every tile is whole rows of
+    16-byte flag vectors (bulk copies of the flags, the agents' row reads)
+    and no smaller than the tile the workspace size assumes."""
+    L = _capi.lib()
+    for dt in (_capi.I32, _capi.F32):
+        assert L.gbscan_num_variants(dt, _capi.KIND_COMPACT) == 4
+        t, i, s, tile = (ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int())
+        for v in range(4):
+            assert L.gbscan_variant_info(dt, _capi.KIND_COMPACT, v, ctypes.byref(t), ctypes.byref(i),
+                                         ctypes.byref(s), ctypes.byref(tile)) == 0
+            helpers = 32 * 2 if v < 3 else 32 * (1 + s.value)
+            assert tile.value == (t.value - helpers) * i.value, v
+            assert tile.value % (16 * 32) == 0 and tile.value >= 256 * 12, v
+            assert i.value % 4 == 0, v
+    assert L.gbscan_num_variants(_capi.I64, _capi.KIND_COMPACT) == 0
+
+
 def test_resident_max_n_arguments():
     L = _capi.lib()
     n = ctypes.c_int64(0)
